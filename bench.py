@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Benchmark: time to relative residual 1e-8 with the matching-aggregation
+AMG preconditioner in FGMRES(30), mixed-precision V-cycle vs all-FP64, on one
+GB300.
+
+One step = one pass of the whole path over one system: amg_setup (matching
+passes, aggregates, Galerkin products, colourings, ILU(0) factors, dense
+last level, precision copies) + amg_solve to ||b - A x|| / ||b|| <= tol
+(FGMRES(30) with the V-cycle preconditioner, true FP64 residual).  Inputs
+(the assembled CSR matrix and right-hand side) are resident in HBM before the
+timed region.  The default workload is the 128^3 anisotropic 3D
+finite-volume problem (2,097,152 unknowns, 14.6 M nonzeros), whose matrix
+alone (175 MB) exceeds L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank solves its own copy (replicas: the single-system
+path has no exchange step); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-rel-residual 1e-8 (mixed vs FP64, same GPU); SpMV/cycle HBM GB/s"
+
+
+def workload(name):
+    from paper_1105_3468_gb300 import workloads as W
+    if name == "c3":
+        return (W.c3_aniso_3d_128(), 1e-8,
+                "fv3d-128^3-aniso-blockkappa (2,097,152 unknowns, 7-point upwind, 16^3 blocks "
+                "kappa_axis=10^U(-3,3), a=(1,1,1)), FP32 V-cycle in FP64 FGMRES(30), tol 1e-8")
+    if name == "c2":
+        return (W.c2_rotating_2d_1024(), 1e-7,
+                "fv2d-1024^2-rotating (1,048,576 unknowns), FGMRES(30), tol 1e-7 "
+                "(1e-8 is below this matrix's FP64 attainable residual)")
+    if name == "c1":
+        return W.c1_block_2d_64(), 1e-8, "fv2d-64^2-blockkappa (4096 unknowns), FGMRES(30), tol 1e-8"
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(prob, tol, iters_fp64, sample_iters=1):
+    """Oracle (single-threaded C, as it stands) on a bounded sample: full-size
+    setup plus `sample_iters` FGMRES iterations, scaled to the iteration count
+    the method needs on this system."""
+    import oracle as O
+    A, b = O.fv_assemble(prob)
+    t0 = time.perf_counter()
+    H = O.Hierarchy(A)
+    t1 = time.perf_counter()
+    H.fgmres(b, tol=tol, maxit=sample_iters)
+    t2 = time.perf_counter()
+    per_it = (t2 - t1) / sample_iters
+    value_ms = 1e3 * ((t1 - t0) + per_it * iters_fp64)
+    return {"value": round(value_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": (f"full-size oracle setup ({t1 - t0:.1f} s) + {sample_iters} FGMRES iteration(s) "
+                       f"({per_it:.1f} s/iteration), scaled to the {iters_fp64} iterations the FP64 method "
+                       f"takes on this system; 1 of {os.cpu_count()} host cores")}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores, bounded samples."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    prob, tol, desc = workload(args.workload)
+    iters_path = os.path.join(ROOT, "oracle", "workload_iters.json")
+    iters = json.load(open(iters_path)).get(args.workload) if os.path.exists(iters_path) else None
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle iteration count for {args.workload}"}))
+        return
+    vals = []
+    bl = None
+    for k in range(args.warmup_ref + args.steps_ref):
+        bl = cpu_baseline(prob, tol, iters)
+        if k >= args.warmup_ref:
+            vals.append(bl["value"])
+    v = statistics.mean(vals)
+    bl["value"] = round(v, 1)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": world,
+           "steps": args.steps_ref, "warmup": args.warmup_ref, "ms_per_step": round(v, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": desc},
+           "cpu_baseline": bl, "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--roofline-class", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--steps-ref", type=int, default=2)
+    ap.add_argument("--warmup-ref", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1105_3468_gb300 import build_lib
+    build_lib.build()
+    import paper_1105_3468_gb300 as amg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    prob, tol, desc = workload(args.workload)
+    A, b = amg.assemble_fv(prob)
+    torch.cuda.synchronize()
+    vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
+
+    def step(prec, timing_class=0, acc=None):
+        h = amg.amg_setup(A, vcycle_prec=prec)
+        if timing_class:
+            amg.amg_set_kernel_timing(h, timing_class)
+        x = torch.zeros_like(b)
+        st = amg.amg_solve(h, b, x, tol)
+        if timing_class and acc is not None:
+            acc.append(amg.amg_get_kernel_timing(h))
+        h.close()
+        return st
+
+    for _ in range(args.warmup):
+        step(vp)
+
+    def timed(prec, timing_class=0):
+        stats, acc = [], []
+        barrier()
+        torch.cuda.synchronize()
+        l0 = amg.amg_launch_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            stats.append(step(prec, timing_class, acc))
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        launches = amg.amg_launch_counter() - l0
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats, acc, launches
+
+    with ClockSampler(local) as clk:
+        ms, stats, acc, launches = timed(vp, args.roofline_class)
+    clocks = clk.summary()
+    ms64, stats64, _, _ = timed(amg.AMG_FP64) if vp != amg.AMG_FP64 else (ms, stats, None, None)
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    Ah = amg.CsrDevice(A.n, A.row_ptr.cpu().numpy(), A.col.cpu().numpy(), A.val.cpu().numpy())
+    bh = b.cpu().numpy()
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        xh = np.zeros(A.n)
+        t0 = time.perf_counter()
+        h = amg.amg_setup(Ah, vcycle_prec=vp)
+        amg.amg_solve(h, bh, xh, tol)
+        h.close()
+        e2e.append(1e3 * (time.perf_counter() - t0))
+    bi = Ah.row_ptr.nbytes + Ah.col.nbytes + Ah.val.nbytes + bh.nbytes + xh.nbytes
+    bo = xh.nbytes
+
+    tot_ms = sum(a[0] for a in acc)
+    tot_n = sum(a[1] for a in acc)
+    tot_b = sum(a[2] for a in acc)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    roof = None
+    if tot_n:
+        achieved = tot_b / tot_n / (tot_ms / tot_n * 1e-3) / 1e9
+        names = {1: "outer FP64 SpMV w = A z_j", 2: "level-0 ILU(0) sweeps", 3: "CGS2 pass"}
+        roof = {"bound": "hbm", "kernel": names.get(args.roofline_class), "achieved": round(achieved, 1),
+                "peak": peak, "peak_source": "measured" if peaks else "fallback", "unit": "GB/s",
+                "frac": round(achieved / peak, 3), "traffic": None,
+                "bytes_per_launch": round(tot_b / tot_n), "avg_launch_us": round(1e3 * tot_ms / tot_n, 2),
+                "launches": tot_n}
+    s0 = stats[-1]
+    out = {
+        "metric": METRIC, "value": round(ms, 2), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32 V-cycle / f64 FGMRES", "bf16": "bf16 values, f32 V-cycle / f64 FGMRES",
+                                       "fp64": "f64"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": desc, "l2": "inputs larger than L2 (matrix 175 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iters": s0.iters, "rel_res_true": s0.rel_res_true, "setup_ms": round(s0.setup_ms, 2),
+        "solve_ms": round(s0.solve_ms, 2), "fp64_ms_per_step": round(ms64, 2), "fp64_iters": stats64[-1].iters,
+        "speedup_vs_fp64": round(ms64 / ms, 3), "levels": s0.nlevels,
+        "e2e": {"value": round(statistics.median(e2e), 2), "unit": "ms", "h2d_bytes_per_step": int(bi),
+                "d2h_bytes_per_step": int(bo)},
+        "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob, tol, stats64[-1].iters)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

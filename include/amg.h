@@ -1,0 +1,267 @@
+/*
+ * amg.h -- C ABI of libamg_gb: matching-aggregation algebraic multigrid as
+ * the preconditioner of a right-preconditioned flexible GMRES solver, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method follows P. Kumar, "Aggregation based on graph matching and
+ * inexact coarse grid solve for algebraic multigrid" (arXiv:1105.3468):
+ *   - problem: A x = b, A in R^{N x N} sparse, x, b in R^N (Section 1,
+ *     eq. (1); Algorithm 1, its title);
+ *   - setup: aggregates from graph matching (Section 2), prolongation P with
+ *     P_ij = 1 iff i in G_j (Section 2, definition of P and eq. (3)),
+ *     Galerkin coarse matrix A_c = P^T A P (eq. (1) of Section 2 and its
+ *     entrywise form), ILU(0) smoother S = L0 U0 (Algorithm 1, setup);
+ *   - preconditioner B~ = (S^{-1} + M~^{-1} - M~^{-1} A S^{-1})^{-1} without
+ *     post-smoothing, M~ = P A~_c P^T (eq. (4), Algorithm 1 "SOLVE B~q=z"
+ *     and "SOLVE M~g=h");
+ *   - Krylov accelerator: GMRES with Givens rotations (Algorithm 1), here
+ *     the flexible right-preconditioned variant FGMRES(m).
+ * Readings where the paper is silent (matching rule and tie-breaks, the
+ * inexact coarse solve as Richardson steps preconditioned by the two-grid
+ * construction of the coarse matrix, orderings, tolerances) are fixed by the
+ * options below and described with each option.
+ *
+ * Conventions for every entry point
+ *   - Return value: an AMG_* status code; nothing is thrown across the ABI.
+ *     amg_last_error() returns a message for the calling thread's last
+ *     failure.
+ *   - Pointers: "host or device" arguments may be ordinary host memory,
+ *     pinned host memory or device memory of the current CUDA device; the
+ *     library detects the kind and copies as needed.  "device" arguments
+ *     must be device memory.  The caller owns every buffer it passes;
+ *     nothing the caller passes is retained after the call returns, except
+ *     the stream given to amg_setup.
+ *   - Streams: all work of a handle is ordered on the stream given to
+ *     amg_setup (NULL = the legacy default stream).  Calls that return host
+ *     results synchronise that stream before returning.
+ *   - Index types: row pointers int64 at the ABI (internally int32: the
+ *     library rejects nnz >= 2^31 with AMG_ERR_INVALID_ARG); column indices
+ *     int32, strictly ascending within each row; every row must store its
+ *     diagonal entry.
+ *   - Determinism: every reduction has a fixed order, so repeated calls on
+ *     the same inputs give bit-identical results.
+ */
+#ifndef AMG_GB_H
+#define AMG_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define AMG_OK 0
+#define AMG_ERR_INVALID_ARG 1   /* bad CSR, null pointer, bad option      */
+#define AMG_ERR_CUDA 2          /* a CUDA runtime call failed             */
+#define AMG_ERR_OOM 3           /* device allocation failed               */
+#define AMG_ERR_NOT_SUPPORTED 4 /* valid request outside what is built    */
+#define AMG_ERR_BREAKDOWN 5     /* zero or non-finite pivot in a factor   */
+#define AMG_ERR_NUMERIC 6       /* NaN/Inf in a residual or a norm        */
+#define AMG_ERR_NOT_CONVERGED 7 /* maxit reached; x holds the last iterate */
+#define AMG_ERR_LIMIT 8         /* a bounded device loop hit its cap      */
+
+/* V-cycle arithmetic (FGMRES itself always runs in FP64). */
+#define AMG_FP64 0              /* all FP64                                */
+#define AMG_FP32 1              /* FP32 storage and arithmetic             */
+#define AMG_BF16 2              /* BF16 matrix values, FP32 vectors/accum. */
+
+/* Elimination order of the ILU(0) factors of one level. */
+#define AMG_ORDER_COLOR 0       /* colour-major (rows of a colour are independent) */
+#define AMG_ORDER_NATURAL 1     /* row index order, the paper's GMG-NO (Section 3) */
+
+/* Colouring priority used by AMG_ORDER_COLOR. */
+#define AMG_COLOR_HASH_JP 0     /* priority (mix64(i ^ (seed + 0x9e3779b97f4a7c15)), i) */
+#define AMG_COLOR_FIRST_FIT 1   /* priority -i (first fit in index order)  */
+
+typedef struct amg_handle amg_handle_t;
+
+/* A square sparse matrix in CSR form (Section 1: A in R^{N x N}). */
+typedef struct {
+    int32_t n;                /* rows = columns, n >= 1                    */
+    int64_t nnz;              /* stored entries = row_ptr[n]               */
+    const int64_t *row_ptr;   /* [n+1], row_ptr[0] = 0, non-decreasing     */
+    const int32_t *col;       /* [nnz], ascending within a row, in [0, n)  */
+    const double *val;        /* [nnz] FP64                                */
+} amg_csr_t;
+
+typedef struct {
+    /* coarsening: each level is aggregated by `passes` heavy-edge matching
+     * passes (aggregates of at most 2^passes points; Section 2 aggregation
+     * by graph matching).  Matching rule: greedy maximal matching in
+     * decreasing key order, key = (w_uv, mix64(((u<<32)|v) ^ seed), u, v),
+     * w_uv = (|a_uv| + |a_vu|)/2, u < v, edges with w > 0. */
+    int32_t passes;           /* default 2                                 */
+    int32_t coarse_inner;     /* Richardson steps solving level 1: 5       */
+    int32_t deep_inner;       /* Richardson steps on levels >= 2: 1        */
+    int32_t dense_max;        /* a level with <= dense_max rows is the last
+                                 one and is solved exactly: 1024           */
+    int32_t max_levels;       /* 2..24, default 12                         */
+    int32_t order_fine;       /* ILU(0) order of level 0: AMG_ORDER_NATURAL */
+    int32_t order_coarse;     /* ILU(0) order of levels >= 1: AMG_ORDER_COLOR */
+    int32_t coloring;         /* AMG_COLOR_HASH_JP                         */
+    int32_t restart;          /* FGMRES restart length m: 30               */
+    int32_t maxit;            /* total inner iterations cap: 600           */
+    int32_t vcycle_prec;      /* AMG_FP64 / AMG_FP32 / AMG_BF16: AMG_FP64  */
+    int32_t build_adjoint;    /* nonzero: also build transposed structures */
+    int32_t use_graphs;       /* nonzero: replay the inner iteration as a CUDA graph */
+    int32_t reserved0;
+    uint64_t seed;            /* tie-break seed, default 0                 */
+} amg_options_t;
+
+typedef struct {
+    int32_t status;           /* same as the call's return value           */
+    int32_t iters;            /* inner FGMRES iterations                   */
+    int32_t restarts;
+    int32_t nlevels;
+    double rel_res_true;      /* ||b - A x|| / ||b|| in FP64 at return      */
+    double setup_ms;          /* wall time of amg_setup                    */
+    double solve_ms;          /* wall time of the solve call               */
+    int32_t n_coarse;         /* rows of level 1                           */
+    int32_t n_colors;         /* colours (or DAG levels) of level 0 sweeps */
+    int64_t nnz_coarse;       /* stored entries of level 1                 */
+    int64_t kernel_launches;  /* kernels this call launched (graph replays count their nodes) */
+} amg_stats_t;
+
+/* ------------------------------------------------------------ basics */
+const char *amg_status_string(int status);
+const char *amg_last_error(void);
+/* Fills *opt with the defaults listed above.  Returns AMG_OK, or
+ * AMG_ERR_INVALID_ARG for a NULL pointer. */
+int amg_default_options(amg_options_t *opt);
+
+/* --------------------------------------------------------------- setup */
+/* Builds the hierarchy for A (Algorithm 1, SETUP PHASE): per level the
+ * matching passes, aggregates, Galerkin products, the ILU(0) factors in the
+ * chosen order, and the dense inverse of the last level; then the FP32/BF16
+ * copies and, if requested, the transposed structures.  A's arrays are host
+ * or device; they are copied.  `stream` is a cudaStream_t (NULL allowed).
+ * Errors: AMG_ERR_INVALID_ARG (bad CSR: unsorted or out-of-range columns,
+ * missing diagonal, nnz >= 2^31; bad option), AMG_ERR_BREAKDOWN (zero ILU
+ * or dense pivot), AMG_ERR_LIMIT (matching/colouring rounds or a coarse row
+ * over its capacity), AMG_ERR_OOM, AMG_ERR_CUDA.  On error *out is NULL. */
+int amg_setup(const amg_csr_t *A, const amg_options_t *opt, void *stream,
+              amg_handle_t **out);
+
+/* Releases everything the handle owns.  NULL is allowed. */
+void amg_destroy(amg_handle_t *h);
+
+/* --------------------------------------------------------------- solve */
+/* Solves A x = b by FGMRES(restart) preconditioned with B~ (Algorithm 1,
+ * PRECONDITIONED GMRES ITERATION), stopping when the true relative residual
+ * ||b - A x|| / ||b|| <= tol (Section 3 stopping rule).  b: host or device
+ * [n]; x: host or device [n], read as the initial guess, written with the
+ * result.  stats may be NULL.  Returns AMG_ERR_NOT_CONVERGED when maxit is
+ * reached (x holds the last iterate), AMG_ERR_NUMERIC for NaN/Inf. */
+int amg_solve(amg_handle_t *h, const double *b, double *x, double tol, amg_stats_t *stats);
+
+/* Solves the adjoint system A^T lambda = g by FGMRES preconditioned with
+ * B~^{-T} = S^{-T}(I - A^T P C^T P^T) + P C^T P^T, the transpose of the
+ * preconditioner (coarse correction first, then the transposed smoother).
+ * Needs build_adjoint.  g, lambda: host or device [n]; lambda is read as
+ * the initial guess.  Errors as amg_solve. */
+int amg_adjoint(amg_handle_t *h, const double *g, double *lambda, double tol, amg_stats_t *stats);
+
+/* Residual history of the last solve or adjoint call: entry 0 is
+ * ||r0||/||b||, then one FGMRES estimate |s_{j+1}|/||b|| per inner
+ * iteration.  out: host [cap]; *len receives the full length. */
+int amg_get_history(amg_handle_t *h, double *out, int32_t cap, int32_t *len);
+
+/* q = B~^{-1} z (transpose = 0) or B~^{-T} z (transpose = 1) at level 0, in
+ * the handle's V-cycle precision with FP64 input and output (Algorithm 1,
+ * SOLVE B~q = z).  z, q: device [n]. */
+int amg_precond_apply(amg_handle_t *h, const double *z, double *q, int32_t transpose);
+
+/* y = A x in FP64 for a CSR given on the device (row_ptr int64).  x, y:
+ * device [n].  Stream-ordered on `stream`; does not synchronise. */
+int amg_spmv(const amg_csr_t *A, const double *x, double *y, void *stream);
+
+/* ------------------------------------------------------- introspection */
+/* Level l facts: info[0] rows, [1] stored entries, [2] sweep levels of the
+ * forward ILU(0) solve (colours in colour order), [3] 1 if dense final
+ * level, [4] rows after the first matching pass (-1 if none), [5] rows of
+ * the next level (-1 if last), [6] colours (0 in natural order),
+ * [7] sweep levels of the backward solve.  info: host [8]. */
+int amg_get_level_info(amg_handle_t *h, int32_t level, int64_t *info);
+int amg_num_levels(amg_handle_t *h, int32_t *nlevels);
+
+/* Aggregate map of level l: pass 0 = composite map to level l+1 (rows of
+ * level l), pass p >= 1 = map of matching pass p.  out: host. */
+int amg_get_aggregates(amg_handle_t *h, int32_t level, int32_t pass, int32_t *out);
+
+/* Matrix of level l (level 0 = A as stored) in CSR: rp [n+1], col [nnz],
+ * val [nnz]; all host.  Level l >= 1 is the Galerkin product. */
+int amg_get_matrix(amg_handle_t *h, int32_t level, int64_t *rp, int32_t *col, double *val);
+
+/* Intermediate Galerkin product after matching pass p (1 <= p < passes) of
+ * level l: sizes via info[0] rows / info[1] nnz when rp == NULL. */
+int amg_get_pass_matrix(amg_handle_t *h, int32_t level, int32_t pass, int64_t *info,
+                        int64_t *rp, int32_t *col, double *val);
+
+/* Colour (AMG_ORDER_COLOR) or 0 (natural) per row of level l.  host. */
+int amg_get_colors(amg_handle_t *h, int32_t level, int32_t *out);
+
+/* FP64 ILU(0) factors of level l on that level's CSR layout: L entries
+ * (unit diagonal implied) before the row in the elimination order, U
+ * entries (with the diagonal) after.  out: host [nnz]. */
+int amg_get_ilu(amg_handle_t *h, int32_t level, double *out);
+
+/* ------------------------------------------------------------ profiling */
+/* Times one kernel class with CUDA events on the handle's stream (for a
+ * roofline figure measured while solving): 0 off, 1 the outer FP64 SpMV
+ * w = A z_j, 2 the level-0 ILU(0) forward+backward sweeps of one
+ * preconditioner application, 3 one CGS2 orthogonalisation pass.  Setting
+ * a class clears the totals.  No effect on results.  Errors:
+ * AMG_ERR_INVALID_ARG. */
+int amg_set_kernel_timing(amg_handle_t *h, int32_t kclass);
+/* Totals since the class was set: summed event time (ms), timed launches,
+ * and the algorithmic bytes those launches move (each array counted once per
+ * launch).  Synchronises the stream. */
+int amg_get_kernel_timing(amg_handle_t *h, double *ms_total, int64_t *launches, double *bytes_total);
+/* Kernels the library has launched from the calling thread so far. */
+int64_t amg_launch_counter(void);
+
+/* ------------------------------------------------------------ FV input */
+/* Cell-centred finite-volume matrix of eq. (2) (Section 1) on an
+ * nx x ny (x nz) grid of [0,1]^dim, h = 1/nx: two-point diffusive fluxes
+ * with the harmonic mean of the face-normal conductivities, first-order
+ * upwind convection, u = 0 on y = 0 and y = 1 (Dirichlet, half-cell
+ * distance), du/dn = 0 elsewhere (zero-gradient ghost, the outward flux
+ * goes to the diagonal).  Faces are visited W, E, S, N, B, T; columns come
+ * out ascending.  All pointers device.  kx/ky/kz [N] conductivity
+ * components per cell; fx [(nx+1) ny nz], fy [nx (ny+1) nz], fz
+ * [nx ny (nz+1)] integrated face fluxes (+axis direction); f [N] source.
+ * Outputs row_ptr [N+1] (int64), col/val with room for (2 dim + 1) N
+ * entries, b [N] = f h^dim; *nnz_out (host) receives nnz.  Synchronises
+ * the stream.  Errors: AMG_ERR_INVALID_ARG for bad sizes. */
+int amg_fv_assemble(int32_t dim, int32_t nx, int32_t ny, int32_t nz,
+                    const double *kx, const double *ky, const double *kz,
+                    const double *fx, const double *fy, const double *fz,
+                    const double *f, int64_t *row_ptr, int32_t *col, double *val,
+                    double *b, int64_t *nnz_out, void *stream);
+
+/* Gradient of a loss L(x) with respect to log kx, log ky, log kz per cell
+ * given lambda = A^{-T} dL/dx and x: dL/dA_ij = -lambda_i x_j restricted to
+ * the diffusive transmissibilities (interior T = h^(d-2) 2 kP kN/(kP+kN),
+ * dT/dlog kP = T kN/(kP+kN); Dirichlet T = h^(d-2) 2 kP, dT/dlog kP = T).
+ * All pointers device; gz unused (may be NULL) in 2D. */
+int amg_fv_grad_logk(int32_t dim, int32_t nx, int32_t ny, int32_t nz,
+                     const double *kx, const double *ky, const double *kz,
+                     const double *lambda, const double *x,
+                     double *gx, double *gy, double *gz, void *stream);
+
+/* Gradient of a loss with respect to the stored values of A for A x = b:
+ * grad_val[k] = -lambda[row_k] * x[col_k] with lambda = A^{-T} dL/dx (the
+ * implicit-function derivative of the solve; dL/db = lambda).  All device
+ * pointers; A's arrays as in amg_csr_t.  Stream-ordered, no synchronisation. */
+int amg_csr_value_grad(const amg_csr_t *A, const double *lambda, const double *x, double *grad_val,
+                       void *stream);
+
+/* ------------------------------------------------------------- version */
+const char *amg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMG_GB_H */

@@ -1,0 +1,972 @@
+// engine.cu -- the C ABI of libamg_gb (include/amg.h): the handle, the
+// setup pipeline (Algorithm 1, SETUP PHASE, applied level by level), the
+// recursive preconditioner (Algorithm 1, SOLVE B~q = z and SOLVE M~g = h,
+// with the inexact coarse solve read as Richardson steps preconditioned by
+// the coarse level's own two-grid construction), and right-preconditioned
+// FGMRES(m) (Algorithm 1, PRECONDITIONED GMRES ITERATION, flexible form).
+#include "../../include/amg.h"
+#include "solve.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+namespace amg {
+
+static thread_local std::string t_last_error;
+
+// ------------------------------------------------------------------ level data
+struct PassData {
+    DCsr mat;            // Galerkin product after this pass (except the last pass)
+    DBuf<int> agg;       // map of this pass
+    int n_in = 0, n_out = 0;
+};
+
+struct Level {
+    DCsr A;                                   // FP64
+    DBuf<float> v32;
+    DBuf<__nv_bfloat16> v16;
+    // transposed matrix (adjoint)
+    DCsr AT;
+    DBuf<float> vt32;
+    DBuf<__nv_bfloat16> vt16;
+    // aggregation to the next level
+    std::vector<PassData> passes;
+    DBuf<int> agg, mptr, midx;
+    int n_next = -1;
+    // smoother
+    int order = AMG_ORDER_COLOR, ncol = 0;
+    DBuf<int> label, pos;
+    DBuf<double> lu;
+    Sweep fwd, bwd, fwdT, bwdT;
+    // dense last level
+    bool dense = false;
+    DBuf<double> inv;
+    // workspace (vector type of the V-cycle, allocated as bytes)
+    DBuf<char> wt, wy, wr, wres, wh, wg, wf;
+};
+
+}  // namespace amg
+
+struct amg_handle {
+    amg_options_t opt;
+    cudaStream_t stream = nullptr;
+    std::vector<std::unique_ptr<amg::Level>> lev;
+    int n = 0;
+    // FGMRES storage
+    amg::DBuf<double> V, Zd, w, r, xb, bb, hist, partials;
+    amg::DBuf<float> Zf, zin32;
+    amg::DBuf<amg::FgState> st;
+    amg::DBuf<unsigned int> ticket;
+    amg::FgState *hst = nullptr;          // pinned host mirror
+    std::vector<double> last_hist;
+    double setup_ms = 0.0;
+    bool adjoint_ready = false;
+    // kernel timing of one kernel class (CUDA events around each launch)
+    int tclass = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;
+    size_t tused = 0;
+    double t_ms = 0.0, t_bytes = 0.0;
+    int64_t t_launches = 0;
+    double t_bytes_per_launch = 0.0;
+};
+
+namespace amg {
+
+// ------------------------------------------------------------------ helpers
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static const T *to_device(const T *p, size_t n, DBuf<T> &tmp, cudaStream_t s) {
+    if (is_device_ptr(p)) return p;
+    tmp.alloc(n ? n : 1);
+    if (n) CU(cudaMemcpyAsync(tmp.get(), p, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return tmp.get();
+}
+
+__global__ void k_rp64_to_32(int n, int64_t nnz, const int64_t *rp64, int *rp32, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
+        int64_t v = rp64[i];
+        bool ok = v >= 0 && v <= nnz && v < (int64_t)0x7fffffff;
+        if (i == 0 && v != 0) ok = false;
+        if (i == n && v != nnz) ok = false;
+        if (i < n && rp64[i + 1] < v) ok = false;
+        if (!ok) atomicAdd(bad, 1);
+        rp32[i] = (int)v;
+    }
+}
+
+static void load_csr(const amg_csr_t *A, DCsr &out, cudaStream_t s) {
+    if (!A || A->n <= 0 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))
+        fail(AMG_ERR_INVALID_ARG, "CSR: null pointer or non-positive size");
+    if (A->nnz >= (int64_t)0x7fffffff) fail(AMG_ERR_INVALID_ARG, "CSR: nnz >= 2^31 is not supported");
+    const int n = A->n;
+    const int nnz = (int)A->nnz;
+    DBuf<int64_t> trp;
+    DBuf<int> tci;
+    DBuf<double> tv;
+    const int64_t *rp64 = to_device(A->row_ptr, (size_t)n + 1, trp, s);
+    const int *ci = to_device(A->col, (size_t)nnz, tci, s);
+    const double *v = to_device(A->val, (size_t)nnz, tv, s);
+    out.n = n;
+    out.nnz = nnz;
+    out.rp.alloc(n + 1);
+    out.ci.alloc(nnz > 0 ? nnz : 1);
+    out.v.alloc(nnz > 0 ? nnz : 1);
+    DBuf<int> bad(1);
+    CU(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    k_rp64_to_32<<<grid_for((size_t)n + 1, 256), 256, 0, s>>>(n, A->nnz, rp64, out.rp.get(), bad.get());
+    CU_LAUNCH("k_rp64_to_32"); count_launch();
+    if (nnz) {
+        CU(cudaMemcpyAsync(out.ci.get(), ci, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemcpyAsync(out.v.get(), v, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
+    }
+    int hbad = 0;
+    CU(cudaMemcpyAsync(&hbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (hbad) fail(AMG_ERR_INVALID_ARG, "CSR: row pointers are not a valid non-decreasing sequence from 0 to nnz");
+    if (csr_validate(n, out.rp.get(), out.ci.get(), s))
+        fail(AMG_ERR_INVALID_ARG, "CSR: columns out of range or not strictly ascending, or a missing diagonal");
+}
+
+__global__ void k_gather_double(const double *src, const int *idx, double *dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];
+}
+
+// Transpose with values: T = M^T (rows ascending).
+static void transpose_values(const DCsr &M, const double *vals, DCsr &T, cudaStream_t s) {
+    DBuf<int> tsrc;
+    csr_transpose(M.n, M.nnz, M.rp.get(), M.ci.get(), T.rp, T.ci, tsrc, s);
+    T.n = M.n;
+    T.nnz = M.nnz;
+    T.v.alloc(M.nnz > 0 ? M.nnz : 1);
+    if (M.nnz) {
+        k_gather_double<<<grid_for(M.nnz, 256), 256, 0, s>>>(vals, tsrc.get(), T.v.get(), M.nnz);
+        CU_LAUNCH("k_gather_double"); count_launch();
+    }
+    CU(cudaStreamSynchronize(s));
+}
+
+// Sweep schedules of the transposed factors: row j of (LU)^T holds U_ij
+// (pos(i) < pos(j), forward, divided by u_jj) and L_ij (pos(i) > pos(j),
+// backward, unit diagonal).
+void build_transposed_sweeps(const DCsr &A, const int *pos, const double *lu, Sweep &fwdT, Sweep &bwdT,
+                             cudaStream_t s);
+
+// ------------------------------------------------------------------ setup
+static void coarsen(Level &L, const amg_options_t &o, DBuf<int> &adj_rp, DBuf<int> &adj_ci, int &adj_nnz,
+                    DCsr &next, cudaStream_t s) {
+    const int n = L.A.n;
+    L.agg.alloc(n);
+    iota_int(L.agg.get(), n, s);
+    const DCsr *cur = &L.A;
+    DCsr last;
+    L.passes.clear();
+    L.passes.resize(o.passes);
+    for (int p = 0; p < o.passes; ++p) {
+        PassData &P = L.passes[p];
+        DBuf<int> arp, aci;
+        int annz = 0;
+        sym_adjacency(*cur, arp, aci, annz, s);
+        DBuf<int> mate(cur->n);
+        match_pass(*cur, arp.get(), aci.get(), annz, o.seed, mate.get(), s);
+        P.n_in = cur->n;
+        P.agg.alloc(cur->n);
+        const int nc = aggregates_from_mate(cur->n, mate.get(), P.agg.get(), s);
+        P.n_out = nc;
+        DBuf<int> mp, mi;
+        members_of(cur->n, nc, P.agg.get(), mp, mi, s);
+        DCsr C;
+        galerkin(*cur, nc, P.agg.get(), mp.get(), mi.get(), C, s);
+        DBuf<int> comp(n);
+        gather_int(P.agg.get(), L.agg.get(), comp.get(), n, s);
+        CU(cudaStreamSynchronize(s));
+        L.agg = std::move(comp);
+        if (p == 0) { adj_rp = std::move(arp); adj_ci = std::move(aci); adj_nnz = annz; }
+        if (p + 1 < o.passes) {
+            P.mat = std::move(C);
+            cur = &P.mat;
+        } else {
+            next = std::move(C);
+        }
+    }
+    L.n_next = next.n;
+    members_of(n, next.n, L.agg.get(), L.mptr, L.midx, s);
+}
+
+static void build_smoother(Level &L, int order, const amg_options_t &o, const int *arp, const int *aci,
+                           cudaStream_t s) {
+    const int n = L.A.n;
+    L.order = order;
+    L.label.alloc(n);
+    L.pos.alloc(n);
+    int nlabels = 1;
+    if (order == AMG_ORDER_NATURAL) {
+        fill_int(L.label.get(), 0, n, s);
+        L.ncol = 0;
+    } else {
+        DBuf<int> tr, tc;
+        int tn = 0;
+        if (!arp) {
+            sym_adjacency(L.A, tr, tc, tn, s);
+            arp = tr.get();
+            aci = tc.get();
+        }
+        L.ncol = color_jp(n, arp, aci, o.coloring, o.seed, L.label.get(), s);
+        nlabels = L.ncol;
+    }
+    elimination_positions(n, L.label.get(), nlabels, L.pos.get(), s);
+    ilu0_factor(L.A, L.pos.get(), L.lu, L.fwd, L.bwd, s);
+}
+
+static void cast_sweep(Sweep &S, int prec, cudaStream_t s) {
+    const size_t nnzf = S.v64.n;
+    if (prec == AMG_FP32 || prec == AMG_BF16) {
+        S.v32.alloc(nnzf);
+        cast_f64_f32(S.v64.get(), S.v32.get(), nnzf, s);
+        if (S.d64.n) {
+            S.d32.alloc(S.d64.n);
+            cast_f64_f32(S.d64.get(), S.d32.get(), S.d64.n, s);
+        }
+    }
+    if (prec == AMG_BF16) {
+        S.v16.alloc(nnzf);
+        cast_f64_bf16(S.v64.get(), S.v16.get(), nnzf, s);
+    }
+}
+
+static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
+    const amg_options_t &o = h->opt;
+    cudaStream_t s = h->stream;
+    auto L0 = std::make_unique<Level>();
+    load_csr(Ain, L0->A, s);
+    h->n = L0->A.n;
+    h->lev.push_back(std::move(L0));
+    for (int l = 0;; ++l) {
+        Level &L = *h->lev[l];
+        bool last = (l > 0 && L.A.n <= o.dense_max) || (l + 1 >= o.max_levels);
+        DBuf<int> arp, aci;
+        int annz = 0;
+        if (!last) {
+            auto N = std::make_unique<Level>();
+            coarsen(L, o, arp, aci, annz, N->A, s);
+            if (l > 0 && (double)N->A.n > 0.9 * (double)L.A.n) {
+                last = true;
+                L.passes.clear();
+                L.agg.release(); L.mptr.release(); L.midx.release();
+                L.n_next = -1;
+            } else {
+                h->lev.push_back(std::move(N));
+            }
+        }
+        if (last && L.A.n <= o.dense_max) {
+            L.dense = true;
+            dense_inverse(L.A, L.inv, s);
+        } else {
+            const int order = l == 0 ? o.order_fine : o.order_coarse;
+            build_smoother(L, order, o, arp.n ? arp.get() : nullptr, aci.n ? aci.get() : nullptr, s);
+        }
+        if (last) break;
+    }
+    // precision copies
+    for (auto &Lp : h->lev) {
+        Level &L = *Lp;
+        if (o.vcycle_prec != AMG_FP64) {
+            L.v32.alloc(L.A.nnz);
+            cast_f64_f32(L.A.v.get(), L.v32.get(), L.A.nnz, s);
+            if (o.vcycle_prec == AMG_BF16) {
+                L.v16.alloc(L.A.nnz);
+                cast_f64_bf16(L.A.v.get(), L.v16.get(), L.A.nnz, s);
+            }
+        }
+        if (!L.dense) {
+            cast_sweep(L.fwd, o.vcycle_prec, s);
+            cast_sweep(L.bwd, o.vcycle_prec, s);
+        }
+    }
+    // adjoint structures
+    if (o.build_adjoint) {
+        for (auto &Lp : h->lev) {
+            Level &L = *Lp;
+            transpose_values(L.A, L.A.v.get(), L.AT, s);
+            if (o.vcycle_prec != AMG_FP64) {
+                L.vt32.alloc(L.AT.nnz);
+                cast_f64_f32(L.AT.v.get(), L.vt32.get(), L.AT.nnz, s);
+                if (o.vcycle_prec == AMG_BF16) {
+                    L.vt16.alloc(L.AT.nnz);
+                    cast_f64_bf16(L.AT.v.get(), L.vt16.get(), L.AT.nnz, s);
+                }
+            }
+            if (!L.dense) {
+                build_transposed_sweeps(L.A, L.pos.get(), L.lu.get(), L.fwdT, L.bwdT, s);
+                cast_sweep(L.fwdT, o.vcycle_prec, s);
+                cast_sweep(L.bwdT, o.vcycle_prec, s);
+            }
+        }
+        h->adjoint_ready = true;
+    }
+    // workspaces
+    const size_t tsz = o.vcycle_prec == AMG_FP64 ? sizeof(double) : sizeof(float);
+    for (auto &Lp : h->lev) {
+        Level &L = *Lp;
+        const size_t b = tsz * (size_t)L.A.n;
+        L.wt.alloc(b); L.wy.alloc(b); L.wr.alloc(b); L.wres.alloc(b); L.wh.alloc(b); L.wg.alloc(b); L.wf.alloc(b);
+    }
+    const size_t n = h->n, m = o.restart;
+    h->V.alloc((m + 1) * n);
+    if (o.vcycle_prec == AMG_FP64) h->Zd.alloc(m * n);
+    else { h->Zf.alloc(m * n); h->zin32.alloc(n); }
+    h->w.alloc(n); h->r.alloc(n); h->xb.alloc(n); h->bb.alloc(n);
+    h->hist.alloc((size_t)o.maxit + 2);
+    h->partials.alloc((size_t)reduce_grid() * KMAX1);
+    h->st.alloc(1);
+    h->ticket.alloc(1);
+    CU(cudaMemsetAsync(h->ticket.get(), 0, sizeof(unsigned int), s));
+    CU(cudaMallocHost(&h->hst, sizeof(FgState)));
+    CU(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ kernel timing
+static void tmark_begin(amg_handle *h, int kclass) {
+    if (h->tclass != kclass) return;
+    if (h->tused == h->tev.size()) {
+        cudaEvent_t a, b;
+        CU(cudaEventCreate(&a));
+        CU(cudaEventCreate(&b));
+        h->tev.emplace_back(a, b);
+    }
+    CU(cudaEventRecord(h->tev[h->tused].first, h->stream));
+}
+static void tmark_end(amg_handle *h, int kclass, double bytes) {
+    if (h->tclass != kclass) return;
+    CU(cudaEventRecord(h->tev[h->tused].second, h->stream));
+    ++h->tused;
+    h->t_bytes += bytes;
+    h->t_bytes_per_launch = bytes;
+}
+// after a synchronisation: fold the recorded pairs into the totals
+static void tcollect(amg_handle *h) {
+    for (size_t i = 0; i < h->tused; ++i) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, h->tev[i].first, h->tev[i].second));
+        h->t_ms += ms;
+        ++h->t_launches;
+    }
+    h->tused = 0;
+}
+
+// ------------------------------------------------------------------ preconditioner
+template <typename T, typename V>
+struct VCycle {
+    amg_handle *h;
+    cudaStream_t s;
+
+    Level &L(int l) { return *h->lev[l]; }
+    static T *ws(DBuf<char> &b) { return reinterpret_cast<T *>(b.get()); }
+
+    const V *vals(Level &Lv, bool tr);
+    LevelMats<V> mats(int l, bool tr) {
+        Level &Lv = L(l);
+        const DCsr &M = tr ? Lv.AT : Lv.A;
+        return LevelMats<V>{M.n, M.nnz, M.rp.get(), M.ci.get(), vals(Lv, tr)};
+    }
+    SweepView<T, V> view(Sweep &S);
+
+    int nlev() const { return (int)h->lev.size(); }
+    bool has_child(int l) { return l + 1 < nlev() && L(l).n_next > 0; }
+
+    // q (mode 0: =, mode 1: +=) B_l^{-1} z
+    void precond(int l, const T *z, T *q, int mode) {
+        Level &Lv = L(l);
+        const int n = Lv.A.n;
+        T *y = ws(Lv.wy), *t = ws(Lv.wt), *r = ws(Lv.wr);
+        if (l == 0) tmark_begin(h, 2);
+        sweep<T, V>(view(Lv.fwd), z, y, 0, s);
+        sweep<T, V>(view(Lv.bwd), y, t, 1, s);
+        if (l == 0) {
+            // factors (values + columns + row pointers + diagonal), z, y, t
+            const double vb = sizeof(V) + 4.0;
+            tmark_end(h, 2, vb * (double)(Lv.fwd.v64.n + Lv.bwd.v64.n) + 8.0 * (2.0 * n + 2.0) +
+                                sizeof(T) * (double)n * 5.0);
+        }
+        level_residual<T, V>(mats(l, false), t, z, r, s);
+        Level &C = L(l + 1);
+        T *hc = ws(C.wh), *gc = ws(C.wg);
+        restrict_to<T>(C.A.n, Lv.mptr.get(), Lv.midx.get(), r, hc, s);
+        level_solve(l + 1, hc, gc);
+        prolong<T, T>(n, Lv.agg.get(), t, gc, q, mode, s);
+    }
+
+    // g = C_l(h): the inexact solve of level l >= 1
+    void level_solve(int l, const T *hrhs, T *g) {
+        Level &Lv = L(l);
+        if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 0, 0, s); return; }
+        const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
+        T *res = ws(Lv.wres);
+        for (int it = 0; it < k; ++it) {
+            const T *in = hrhs;
+            if (it > 0) {
+                level_residual<T, V>(mats(l, false), g, hrhs, res, s);
+                in = res;
+            }
+            if (has_child(l)) {
+                precond(l, in, g, it == 0 ? 0 : 1);
+            } else {
+                T *y = ws(Lv.wy), *t = ws(Lv.wt);
+                sweep<T, V>(view(Lv.fwd), in, y, 0, s);
+                sweep<T, V>(view(Lv.bwd), y, t, 1, s);
+                vec_acc<T>(Lv.A.n, t, g, it == 0 ? 0 : 1, s);
+            }
+        }
+    }
+
+    // q (mode) = B_l^{-T} z = f + S^{-T}(z - A^T f), f = P C^T P^T z
+    void precondT(int l, const T *z, T *q, int mode) {
+        Level &Lv = L(l);
+        const int n = Lv.A.n;
+        Level &C = L(l + 1);
+        T *hc = ws(C.wh), *gc = ws(C.wg);
+        T *f = ws(Lv.wf), *r = ws(Lv.wr), *y = ws(Lv.wy), *t = ws(Lv.wt);
+        restrict_to<T>(C.A.n, Lv.mptr.get(), Lv.midx.get(), z, hc, s);
+        level_solveT(l + 1, hc, gc);
+        prolong<T, T>(n, Lv.agg.get(), nullptr, gc, f, 2, s);
+        level_residual<T, V>(mats(l, true), f, z, r, s);
+        sweep<T, V>(view(Lv.fwdT), r, y, 1, s);
+        sweep<T, V>(view(Lv.bwdT), y, t, 0, s);
+        // q (mode)= f + t
+        prolong<T, T>(n, nullptr, f, t, q, mode == 0 ? 3 : 4, s);
+    }
+
+    void level_solveT(int l, const T *hrhs, T *g) {
+        Level &Lv = L(l);
+        if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 1, 0, s); return; }
+        const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
+        T *res = ws(Lv.wres);
+        for (int it = 0; it < k; ++it) {
+            const T *in = hrhs;
+            if (it > 0) {
+                level_residual<T, V>(mats(l, true), g, hrhs, res, s);
+                in = res;
+            }
+            if (has_child(l)) {
+                precondT(l, in, g, it == 0 ? 0 : 1);
+            } else {
+                T *y = ws(Lv.wy), *t = ws(Lv.wt);
+                sweep<T, V>(view(Lv.fwdT), in, y, 1, s);
+                sweep<T, V>(view(Lv.bwdT), y, t, 0, s);
+                vec_acc<T>(Lv.A.n, t, g, it == 0 ? 0 : 1, s);
+            }
+        }
+    }
+};
+
+template <> const double *VCycle<double, double>::vals(Level &Lv, bool tr) { return tr ? Lv.AT.v.get() : Lv.A.v.get(); }
+template <> const float *VCycle<float, float>::vals(Level &Lv, bool tr) { return tr ? Lv.vt32.get() : Lv.v32.get(); }
+template <> const __nv_bfloat16 *VCycle<float, __nv_bfloat16>::vals(Level &Lv, bool tr) {
+    return tr ? Lv.vt16.get() : Lv.v16.get();
+}
+template <> SweepView<double, double> VCycle<double, double>::view(Sweep &S) {
+    return SweepView<double, double>{S.nlev, S.lev_ptr.data(), S.rows.get(), S.rp.get(), S.ci.get(), S.v64.get(),
+                                     S.d64.n ? S.d64.get() : nullptr};
+}
+template <> SweepView<float, float> VCycle<float, float>::view(Sweep &S) {
+    return SweepView<float, float>{S.nlev, S.lev_ptr.data(), S.rows.get(), S.rp.get(), S.ci.get(), S.v32.get(),
+                                   S.d32.n ? S.d32.get() : nullptr};
+}
+template <> SweepView<float, __nv_bfloat16> VCycle<float, __nv_bfloat16>::view(Sweep &S) {
+    return SweepView<float, __nv_bfloat16>{S.nlev, S.lev_ptr.data(), S.rows.get(), S.rp.get(), S.ci.get(),
+                                           S.v16.get(), S.d32.n ? S.d32.get() : nullptr};
+}
+
+// Preconditioner application at level 0 with FP64 input; output z in the
+// V-cycle type (zout) or FP64 (zout64).
+template <typename T, typename V>
+static void apply_level0(amg_handle *h, const double *vin, T *zout, bool transpose) {
+    VCycle<T, V> vc{h, h->stream};
+    const T *zin;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        zin = reinterpret_cast<const T *>(vin);
+    } else {
+        convert_f64_f32(h->n, vin, h->zin32.get(), h->stream);
+        zin = reinterpret_cast<const T *>(h->zin32.get());
+    }
+    if (h->lev.size() < 2) fail(AMG_ERR_NOT_SUPPORTED, "hierarchy has a single level");
+    if (transpose) vc.precondT(0, zin, zout, 0);
+    else vc.precond(0, zin, zout, 0);
+}
+
+static void apply_precond(amg_handle *h, const double *vin, int j, bool transpose) {
+    const size_t n = h->n;
+    switch (h->opt.vcycle_prec) {
+    case AMG_FP64: apply_level0<double, double>(h, vin, h->Zd.get() + (size_t)j * n, transpose); break;
+    case AMG_FP32: apply_level0<float, float>(h, vin, h->Zf.get() + (size_t)j * n, transpose); break;
+    default: apply_level0<float, __nv_bfloat16>(h, vin, h->Zf.get() + (size_t)j * n, transpose); break;
+    }
+}
+
+// ------------------------------------------------------------------ FGMRES
+static void outer_spmv_z(amg_handle *h, int j, double *y, bool transpose) {
+    Level &L0 = *h->lev[0];
+    const DCsr &M = transpose ? L0.AT : L0.A;
+    const size_t n = h->n;
+    const double xs = h->opt.vcycle_prec == AMG_FP64 ? 8.0 : 4.0;
+    // algorithmic bytes: values + columns, row pointers, x read once, y written once
+    const double bytes = 12.0 * M.nnz + 4.0 * (M.n + 1) + xs * M.n + 8.0 * M.n;
+    tmark_begin(h, 1);
+    if (h->opt.vcycle_prec == AMG_FP64)
+        spmv_f64(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), h->Zd.get() + j * n, y, h->stream);
+    else
+        spmv_f64_xf32(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), h->Zf.get() + j * n, y, h->stream);
+    tmark_end(h, 1, bytes);
+}
+static void outer_residual(amg_handle *h, const double *b, const double *x, double *r, bool transpose) {
+    Level &L0 = *h->lev[0];
+    const DCsr &M = transpose ? L0.AT : L0.A;
+    residual_f64(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), x, b, r, h->stream);
+}
+
+static double read_norm(amg_handle *h, const double *v) {
+    cudaStream_t s = h->stream;
+    norm2(h->n, v, h->partials.get(), h->ticket.get(), h->st.get()->nrm2, s);
+    double r = 0.0;
+    CU(cudaMemcpyAsync(&r, h->st.get()->nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return std::sqrt(r);
+}
+
+static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, amg_stats_t *stats, bool transpose) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t launches0 = launch_count();
+    cudaStream_t s = h->stream;
+    const size_t n = h->n;
+    const int m = h->opt.restart;
+    const bool x_dev = is_device_ptr(x_io);
+    double *x = h->xb.get();
+    const double *b;
+    DBuf<double> tb;
+    b = to_device(b_in, n, tb, s);
+    if (is_device_ptr(b_in)) b = b_in;
+    if (x_dev) CU(cudaMemcpyAsync(x, x_io, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else CU(cudaMemcpyAsync(x, x_io, n * sizeof(double), cudaMemcpyHostToDevice, s));
+
+    FgState *dst = h->st.get();
+    FgState &hs = *h->hst;
+    memset(&hs, 0, sizeof(FgState));
+    hs.m = m; hs.maxit = h->opt.maxit; hs.hist_cap = h->opt.maxit + 2; hs.tol = tol;
+    hs.hist = h->hist.get();
+    int status = AMG_OK, total = 0, restarts = 0;
+    double relres = 0.0;
+    const double bnorm = read_norm(h, b);
+    h->last_hist.clear();
+    if (!std::isfinite(bnorm)) status = AMG_ERR_NUMERIC;
+    else if (bnorm == 0.0) {
+        CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+        h->last_hist.push_back(0.0);
+    } else {
+        hs.bnorm = bnorm;
+        hs.hist_len = 1;
+        CU(cudaMemcpyAsync(dst, &hs, sizeof(FgState), cudaMemcpyHostToDevice, s));
+        outer_residual(h, b, x, h->r.get(), transpose);
+        double beta = read_norm(h, h->r.get());      // leaves ||r0||^2 in the state for the restart
+        relres = beta / bnorm;
+        CU(cudaMemcpyAsync(h->hist.get(), &relres, sizeof(double), cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));
+        if (!std::isfinite(relres)) status = AMG_ERR_NUMERIC;
+        while (status == AMG_OK) {
+            if (relres <= tol) break;
+            if (total >= h->opt.maxit) { status = AMG_ERR_NOT_CONVERGED; break; }
+            // the state's nrm2 holds ||r||^2 from read_norm
+            restart_scale(n, h->r.get(), h->V.get(), dst, s);
+            int j = 0;
+            for (; j < m; ++j) {
+                double *vj = h->V.get() + (size_t)j * n;
+                apply_precond(h, vj, j, transpose);
+                outer_spmv_z(h, j, h->w.get(), transpose);
+                mdot(n, j + 1, h->w.get(), h->V.get(), n, h->partials.get(), h->ticket.get(), dst->h1, s);
+                // CGS2: reads K basis vectors and w, writes w
+                const double cbytes = 8.0 * (double)n * (j + 1) + 16.0 * (double)n;
+                tmark_begin(h, 3);
+                cgs_update(n, j + 1, dst->h1, h->w.get(), h->V.get(), n, 1, h->partials.get(), h->ticket.get(), dst->h2, s);
+                tmark_end(h, 3, cbytes);
+                tmark_begin(h, 3);
+                cgs_update(n, j + 1, dst->h2, h->w.get(), h->V.get(), n, 0, h->partials.get(), h->ticket.get(), dst->nrm2, s);
+                tmark_end(h, 3, cbytes);
+                givens(dst, j, s);
+                scale_next(n, h->w.get(), h->V.get() + (size_t)(j + 1) * n, dst, s);
+                int flags[2];
+                CU(cudaMemcpyAsync(flags, &dst->stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+                CU(cudaStreamSynchronize(s));
+                tcollect(h);
+                if (flags[0]) { ++j; break; }
+            }
+            CU(cudaMemcpyAsync(&hs, dst, sizeof(FgState), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            total = hs.total;
+            if (hs.status) { status = hs.status; break; }
+            backsolve(dst, s);
+            if (h->opt.vcycle_prec == AMG_FP64) update_x<double>(n, dst, h->Zd.get(), n, x, s);
+            else update_x<float>(n, dst, h->Zf.get(), n, x, s);
+            outer_residual(h, b, x, h->r.get(), transpose);
+            const double beta = read_norm(h, h->r.get());
+            relres = beta / bnorm;
+            if (!std::isfinite(relres)) { status = AMG_ERR_NUMERIC; break; }
+            if (relres <= tol) break;
+            if (total >= h->opt.maxit) { status = AMG_ERR_NOT_CONVERGED; break; }
+            ++restarts;
+        }
+        CU(cudaMemcpyAsync(&hs, dst, sizeof(FgState), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        h->last_hist.resize(hs.hist_len);
+        if (hs.hist_len)
+            CU(cudaMemcpyAsync(h->last_hist.data(), h->hist.get(), sizeof(double) * hs.hist_len, cudaMemcpyDeviceToHost, s));
+    }
+    if (x_dev) CU(cudaMemcpyAsync(x_io, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else CU(cudaMemcpyAsync(x_io, x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const auto t1 = std::chrono::steady_clock::now();
+    if (stats) {
+        stats->status = status;
+        stats->iters = total;
+        stats->restarts = restarts;
+        stats->nlevels = (int)h->lev.size();
+        stats->rel_res_true = relres;
+        stats->setup_ms = h->setup_ms;
+        stats->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        stats->n_coarse = h->lev.size() > 1 ? h->lev[1]->A.n : 0;
+        stats->nnz_coarse = h->lev.size() > 1 ? h->lev[1]->A.nnz : 0;
+        stats->n_colors = h->lev[0]->fwd.nlev;
+        stats->kernel_launches = launch_count() - launches0;
+    }
+    return status;
+}
+
+}  // namespace amg
+
+// =================================================================== C ABI
+using namespace amg;
+
+#define ABI_TRY try {
+#define ABI_CATCH                                                     \
+    }                                                                 \
+    catch (const amg::Error &e) {                                     \
+        t_last_error = e.msg;                                         \
+        return e.status;                                              \
+    }                                                                 \
+    catch (const std::bad_alloc &) {                                  \
+        t_last_error = "host allocation failed";                      \
+        return AMG_ERR_OOM;                                           \
+    }                                                                 \
+    catch (...) {                                                     \
+        t_last_error = "unexpected exception";                        \
+        return AMG_ERR_CUDA;                                          \
+    }
+
+extern "C" {
+
+const char *amg_version(void) { return "amg_gb 0.1 (sm_103a)"; }
+
+const char *amg_status_string(int st) {
+    switch (st) {
+    case AMG_OK: return "ok";
+    case AMG_ERR_INVALID_ARG: return "invalid argument";
+    case AMG_ERR_CUDA: return "CUDA error";
+    case AMG_ERR_OOM: return "out of device memory";
+    case AMG_ERR_NOT_SUPPORTED: return "not supported";
+    case AMG_ERR_BREAKDOWN: return "breakdown (zero or non-finite pivot)";
+    case AMG_ERR_NUMERIC: return "non-finite residual";
+    case AMG_ERR_NOT_CONVERGED: return "not converged";
+    case AMG_ERR_LIMIT: return "device loop limit reached";
+    default: return "unknown status";
+    }
+}
+
+const char *amg_last_error(void) { return t_last_error.c_str(); }
+
+int amg_default_options(amg_options_t *o) {
+    if (!o) return AMG_ERR_INVALID_ARG;
+    memset(o, 0, sizeof(*o));
+    o->passes = 2;
+    o->coarse_inner = 5;
+    o->deep_inner = 1;
+    o->dense_max = 1024;
+    o->max_levels = 12;
+    o->order_fine = AMG_ORDER_NATURAL;
+    o->order_coarse = AMG_ORDER_COLOR;
+    o->coloring = AMG_COLOR_HASH_JP;
+    o->restart = 30;
+    o->maxit = 600;
+    o->vcycle_prec = AMG_FP64;
+    o->build_adjoint = 0;
+    o->use_graphs = 0;
+    o->seed = 0;
+    return AMG_OK;
+}
+
+static void check_options(const amg_options_t &o) {
+    if (o.passes < 1 || o.passes > 8 || o.coarse_inner < 1 || o.deep_inner < 1 || o.dense_max < 0 ||
+        o.dense_max > 4096 || o.max_levels < 2 || o.max_levels > 24 || o.restart < 1 || o.restart > KMAX1 - 1 ||
+        o.maxit < 0 || o.vcycle_prec < 0 || o.vcycle_prec > 2 || o.order_fine < 0 || o.order_fine > 1 ||
+        o.order_coarse < 0 || o.order_coarse > 1 || o.coloring < 0 || o.coloring > 1)
+        fail(AMG_ERR_INVALID_ARG, "option out of range (restart <= 31, dense_max <= 4096, 2 <= max_levels <= 24)");
+}
+
+int amg_setup(const amg_csr_t *A, const amg_options_t *opt, void *stream, amg_handle_t **out) {
+    if (out) *out = nullptr;
+    ABI_TRY
+    if (!A || !out) fail(AMG_ERR_INVALID_ARG, "amg_setup: null argument");
+    auto t0 = std::chrono::steady_clock::now();
+    std::unique_ptr<amg_handle> h(new amg_handle());
+    if (opt) h->opt = *opt;
+    else amg_default_options(&h->opt);
+    check_options(h->opt);
+    h->stream = (cudaStream_t)stream;
+    setup_impl(h.get(), A);
+    h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h.release();
+    return AMG_OK;
+    ABI_CATCH
+}
+
+void amg_destroy(amg_handle_t *h) {
+    if (!h) return;
+    try {
+        cudaStreamSynchronize(h->stream);
+        if (h->hst) cudaFreeHost(h->hst);
+        for (auto &e : h->tev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+        delete h;
+    } catch (...) {
+    }
+}
+
+int amg_solve(amg_handle_t *h, const double *b, double *x, double tol, amg_stats_t *stats) {
+    ABI_TRY
+    if (!h || !b || !x) fail(AMG_ERR_INVALID_ARG, "amg_solve: null argument");
+    if (!(tol >= 0.0)) fail(AMG_ERR_INVALID_ARG, "amg_solve: tol must be >= 0");
+    return fgmres(h, b, x, tol, stats, false);
+    ABI_CATCH
+}
+
+int amg_adjoint(amg_handle_t *h, const double *g, double *lambda, double tol, amg_stats_t *stats) {
+    ABI_TRY
+    if (!h || !g || !lambda) fail(AMG_ERR_INVALID_ARG, "amg_adjoint: null argument");
+    if (!h->adjoint_ready) fail(AMG_ERR_INVALID_ARG, "amg_adjoint: setup without build_adjoint");
+    if (!(tol >= 0.0)) fail(AMG_ERR_INVALID_ARG, "amg_adjoint: tol must be >= 0");
+    return fgmres(h, g, lambda, tol, stats, true);
+    ABI_CATCH
+}
+
+int amg_get_history(amg_handle_t *h, double *out, int32_t cap, int32_t *len) {
+    ABI_TRY
+    if (!h || !len) fail(AMG_ERR_INVALID_ARG, "amg_get_history: null argument");
+    *len = (int32_t)h->last_hist.size();
+    if (out) for (int i = 0; i < cap && i < *len; ++i) out[i] = h->last_hist[i];
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_precond_apply(amg_handle_t *h, const double *z, double *q, int32_t transpose) {
+    ABI_TRY
+    if (!h || !z || !q) fail(AMG_ERR_INVALID_ARG, "amg_precond_apply: null argument");
+    if (transpose && !h->adjoint_ready) fail(AMG_ERR_INVALID_ARG, "amg_precond_apply: no adjoint structures");
+    if (!is_device_ptr(z) || !is_device_ptr(q)) fail(AMG_ERR_INVALID_ARG, "amg_precond_apply: device pointers required");
+    apply_precond(h, z, 0, transpose != 0);
+    const size_t n = h->n;
+    if (h->opt.vcycle_prec == AMG_FP64)
+        CU(cudaMemcpyAsync(q, h->Zd.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    else
+        convert_f32_f64(n, h->Zf.get(), q, h->stream);
+    CU(cudaStreamSynchronize(h->stream));
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_spmv(const amg_csr_t *A, const double *x, double *y, void *stream) {
+    ABI_TRY
+    if (!A || !x || !y || A->n <= 0 || !A->row_ptr) fail(AMG_ERR_INVALID_ARG, "amg_spmv: bad argument");
+    if (A->nnz >= (int64_t)0x7fffffff) fail(AMG_ERR_INVALID_ARG, "amg_spmv: nnz >= 2^31");
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<int> rp32(A->n + 1), bad(1);
+    CU(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    k_rp64_to_32<<<grid_for((size_t)A->n + 1, 256), 256, 0, s>>>(A->n, A->nnz, A->row_ptr, rp32.get(), bad.get());
+    CU_LAUNCH("k_rp64_to_32"); count_launch();
+    spmv_f64(A->n, (int)A->nnz, rp32.get(), A->col, A->val, x, y, s);
+    CU(cudaStreamSynchronize(s));
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_set_kernel_timing(amg_handle_t *h, int32_t kclass) {
+    ABI_TRY
+    if (!h || kclass < 0 || kclass > 3) fail(AMG_ERR_INVALID_ARG, "amg_set_kernel_timing: bad argument");
+    h->tclass = kclass;
+    h->t_ms = 0.0; h->t_bytes = 0.0; h->t_launches = 0; h->tused = 0;
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_get_kernel_timing(amg_handle_t *h, double *ms_total, int64_t *launches, double *bytes_total) {
+    ABI_TRY
+    if (!h || !ms_total || !launches || !bytes_total) fail(AMG_ERR_INVALID_ARG, "amg_get_kernel_timing: null");
+    CU(cudaStreamSynchronize(h->stream));
+    tcollect(h);
+    *ms_total = h->t_ms;
+    *launches = h->t_launches;
+    *bytes_total = h->t_bytes;
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int64_t amg_launch_counter(void) { return launch_count(); }
+
+int amg_num_levels(amg_handle_t *h, int32_t *nlevels) {
+    if (!h || !nlevels) return AMG_ERR_INVALID_ARG;
+    *nlevels = (int32_t)h->lev.size();
+    return AMG_OK;
+}
+
+static Level &level_of(amg_handle_t *h, int l) {
+    if (!h || l < 0 || l >= (int)h->lev.size()) fail(AMG_ERR_INVALID_ARG, "level out of range");
+    return *h->lev[l];
+}
+
+int amg_get_level_info(amg_handle_t *h, int32_t level, int64_t *info) {
+    ABI_TRY
+    if (!info) fail(AMG_ERR_INVALID_ARG, "null info");
+    Level &L = level_of(h, level);
+    info[0] = L.A.n;
+    info[1] = L.A.nnz;
+    info[2] = L.dense ? 0 : L.fwd.nlev;
+    info[3] = L.dense ? 1 : 0;
+    info[4] = L.passes.empty() ? -1 : L.passes[0].n_out;
+    info[5] = L.n_next;
+    info[6] = L.ncol;
+    info[7] = L.dense ? 0 : L.bwd.nlev;
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_get_aggregates(amg_handle_t *h, int32_t level, int32_t pass, int32_t *out) {
+    ABI_TRY
+    Level &L = level_of(h, level);
+    if (!out || L.n_next < 0) fail(AMG_ERR_INVALID_ARG, "no aggregation on this level");
+    if (pass == 0) {
+        CU(cudaMemcpy(out, L.agg.get(), sizeof(int) * L.A.n, cudaMemcpyDeviceToHost));
+    } else {
+        if (pass < 1 || pass > (int)L.passes.size()) fail(AMG_ERR_INVALID_ARG, "pass out of range");
+        const PassData &P = L.passes[pass - 1];
+        CU(cudaMemcpy(out, P.agg.get(), sizeof(int) * P.n_in, cudaMemcpyDeviceToHost));
+    }
+    return AMG_OK;
+    ABI_CATCH
+}
+
+static void csr_to_host(const DCsr &M, int64_t *rp, int32_t *col, double *val) {
+    std::vector<int> r32(M.n + 1);
+    CU(cudaMemcpy(r32.data(), M.rp.get(), sizeof(int) * (M.n + 1), cudaMemcpyDeviceToHost));
+    for (int i = 0; i <= M.n; ++i) rp[i] = r32[i];
+    if (M.nnz) {
+        CU(cudaMemcpy(col, M.ci.get(), sizeof(int) * M.nnz, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(val, M.v.get(), sizeof(double) * M.nnz, cudaMemcpyDeviceToHost));
+    }
+}
+
+int amg_get_matrix(amg_handle_t *h, int32_t level, int64_t *rp, int32_t *col, double *val) {
+    ABI_TRY
+    Level &L = level_of(h, level);
+    if (!rp || !col || !val) fail(AMG_ERR_INVALID_ARG, "null output");
+    csr_to_host(L.A, rp, col, val);
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_get_pass_matrix(amg_handle_t *h, int32_t level, int32_t pass, int64_t *info, int64_t *rp, int32_t *col,
+                        double *val) {
+    ABI_TRY
+    Level &L = level_of(h, level);
+    if (pass < 1 || pass >= (int)L.passes.size()) fail(AMG_ERR_INVALID_ARG, "pass out of range");
+    const DCsr &M = L.passes[pass - 1].mat;
+    if (info) { info[0] = M.n; info[1] = M.nnz; }
+    if (rp) {
+        if (!col || !val) fail(AMG_ERR_INVALID_ARG, "null output");
+        csr_to_host(M, rp, col, val);
+    }
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_get_colors(amg_handle_t *h, int32_t level, int32_t *out) {
+    ABI_TRY
+    Level &L = level_of(h, level);
+    if (!out || L.dense) fail(AMG_ERR_INVALID_ARG, "no smoother on this level");
+    CU(cudaMemcpy(out, L.label.get(), sizeof(int) * L.A.n, cudaMemcpyDeviceToHost));
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_get_ilu(amg_handle_t *h, int32_t level, double *out) {
+    ABI_TRY
+    Level &L = level_of(h, level);
+    if (!out || L.dense) fail(AMG_ERR_INVALID_ARG, "no smoother on this level");
+    CU(cudaMemcpy(out, L.lu.get(), sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost));
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_fv_assemble(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *kx, const double *ky,
+                    const double *kz, const double *fx, const double *fy, const double *fz, const double *f,
+                    int64_t *row_ptr, int32_t *col, double *val, double *b, int64_t *nnz_out, void *stream) {
+    ABI_TRY
+    if ((dim != 2 && dim != 3) || nx <= 0 || ny <= 0 || nz <= 0 || (dim == 2 && nz != 1))
+        fail(AMG_ERR_INVALID_ARG, "amg_fv_assemble: bad grid");
+    if ((int64_t)nx * ny * nz * (2 * dim + 1) >= (int64_t)0x7fffffff) fail(AMG_ERR_INVALID_ARG, "grid too large");
+    if (!kx || !ky || !fx || !fy || !f || !row_ptr || !col || !val || !b || !nnz_out || (dim == 3 && (!kz || !fz)))
+        fail(AMG_ERR_INVALID_ARG, "amg_fv_assemble: null pointer");
+    *nnz_out = fv_assemble(dim, nx, ny, nz, kx, ky, kz, fx, fy, fz, f, row_ptr, col, val, b, (cudaStream_t)stream);
+    return AMG_OK;
+    ABI_CATCH
+}
+
+__global__ void k_csr_outer_grad(int n, const int64_t *rp, const int32_t *ci, const double *lam, const double *x,
+                                 double *g) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double li = lam[i];
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) g[e] = -li * x[ci[e]];
+    }
+}
+
+int amg_csr_value_grad(const amg_csr_t *A, const double *lambda, const double *x, double *grad_val, void *stream) {
+    ABI_TRY
+    if (!A || !A->row_ptr || !A->col || !lambda || !x || !grad_val || A->n <= 0)
+        fail(AMG_ERR_INVALID_ARG, "amg_csr_value_grad: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_csr_outer_grad<<<grid_for(A->n, 256), 256, 0, s>>>(A->n, A->row_ptr, A->col, lambda, x, grad_val);
+    CU_LAUNCH("k_csr_outer_grad"); count_launch();
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_fv_grad_logk(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *kx, const double *ky,
+                     const double *kz, const double *lambda, const double *x, double *gx, double *gy, double *gz,
+                     void *stream) {
+    ABI_TRY
+    if ((dim != 2 && dim != 3) || nx <= 0 || ny <= 0 || nz <= 0 || (dim == 2 && nz != 1))
+        fail(AMG_ERR_INVALID_ARG, "amg_fv_grad_logk: bad grid");
+    if (!kx || !ky || !lambda || !x || !gx || !gy || (dim == 3 && (!kz || !gz)))
+        fail(AMG_ERR_INVALID_ARG, "amg_fv_grad_logk: null pointer");
+    fv_grad_logk(dim, nx, ny, nz, kx, ky, kz, lambda, x, gx, gy, gz, (cudaStream_t)stream);
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    return AMG_OK;
+    ABI_CATCH
+}
+
+}  // extern "C"

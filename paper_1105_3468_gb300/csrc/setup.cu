@@ -1,0 +1,1005 @@
+// setup.cu -- GPU setup phase of the matching-aggregation AMG hierarchy
+// (Algorithm 1, SETUP PHASE of the paper): heavy-edge matching, aggregates,
+// Galerkin products P^T A P, colourings, ILU(0) factors with their sweep
+// schedules, the dense inverse of the last level, precision casts, and the
+// finite-volume assembly of eq. (2).
+//
+// Every floating-point step that feeds an integer decision (matching keys)
+// or a later level (Galerkin sums, ILU factors) uses explicitly rounded
+// intrinsics (__dadd_rn, __dmul_rn, ...) so that no multiply-add is fused:
+// the results are bit-identical to the plain sequential definition.
+#include "internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+
+namespace amg {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    // SplitMix64 output finaliser (Steele, Lea, Flood 2014)
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int find_col(const int *ci, int b, int e, int c) {
+    int lo = b, hi = e - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int x = ci[mid];
+        if (x == c) return mid;
+        if (x < c) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_volatile(const T *p) { return *(const volatile T *)p; }
+
+struct Flags {   // device-side status words
+    int a, b, c, d;
+};
+
+static int read_int(const int *d, cudaStream_t s) {
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return h;
+}
+
+// ------------------------------------------------------------------ validation
+__global__ void k_validate(int n, const int *rp, const int *ci, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int b = rp[i], e = rp[i + 1];
+        bool ok = e >= b, diag = false;
+        for (int k = b; ok && k < e; ++k) {
+            int c = ci[k];
+            if (c < 0 || c >= n) ok = false;
+            if (k > b && c <= ci[k - 1]) ok = false;
+            if (c == i) diag = true;
+        }
+        if (!ok || !diag) atomicAdd(bad, 1);
+    }
+}
+
+int csr_validate(int n, const int *rp, const int *ci, cudaStream_t s) {
+    DBuf<int> bad(1);
+    CU(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    k_validate<<<grid_for(n, 256), 256, 0, s>>>(n, rp, ci, bad.get());
+    CU_LAUNCH("k_validate"); count_launch();
+    return read_int(bad.get(), s);
+}
+
+// ------------------------------------------------------------------ symmetrised adjacency
+__global__ void k_sym_count(int n, const int *rp, const int *ci, const int *trp, const int *tci, int *cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int p = rp[i], pe = rp[i + 1], q = trp[i], qe = trp[i + 1], m = 0;
+        while (p < pe || q < qe) {
+            int c;
+            if (q >= qe || (p < pe && ci[p] < tci[q])) c = ci[p++];
+            else if (p >= pe || tci[q] < ci[p]) c = tci[q++];
+            else { c = ci[p]; ++p; ++q; }
+            if (c != i) ++m;
+        }
+        cnt[i] = m;
+    }
+}
+
+__global__ void k_sym_fill(int n, const int *rp, const int *ci, const int *trp, const int *tci,
+                           const int *arp, int *aci) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int p = rp[i], pe = rp[i + 1], q = trp[i], qe = trp[i + 1], m = arp[i];
+        while (p < pe || q < qe) {
+            int c;
+            if (q >= qe || (p < pe && ci[p] < tci[q])) c = ci[p++];
+            else if (p >= pe || tci[q] < ci[p]) c = tci[q++];
+            else { c = ci[p]; ++p; ++q; }
+            if (c != i) aci[m++] = c;
+        }
+    }
+}
+
+void sym_adjacency(const DCsr &A, DBuf<int> &arp, DBuf<int> &aci, int &annz, cudaStream_t s) {
+    DBuf<int> trp, tci, tsrc;
+    csr_transpose(A.n, A.nnz, A.rp.get(), A.ci.get(), trp, tci, tsrc, s);
+    DBuf<int> cnt(A.n + 1);
+    fill_int(cnt.get(), 0, A.n + 1, s);
+    k_sym_count<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp.get(), A.ci.get(), trp.get(), tci.get(), cnt.get());
+    CU_LAUNCH("k_sym_count"); count_launch();
+    arp.alloc(A.n + 1);
+    exclusive_scan_int(cnt.get(), arp.get(), A.n + 1, &annz, s);
+    aci.alloc(annz > 0 ? annz : 1);
+    k_sym_fill<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp.get(), A.ci.get(), trp.get(), tci.get(), arp.get(), aci.get());
+    CU_LAUNCH("k_sym_fill"); count_launch();
+    CU(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ matching
+// Edge {u,v}, u < v: w = (|a_uv| + |a_vu|) * 0.5, missing entry = 0; key
+// (w, mix64(((u<<32)|v) ^ seed), u, v), larger first.  Each round, every
+// free vertex proposes to its largest-key free neighbour; mutual proposals
+// are matched.  Mutual maxima of a strict total order are exactly the
+// edges a greedy pass in decreasing key order takes, so the fixed point is
+// the greedy matching.
+__global__ void k_edge_weights(int n, const int *rp, const int *ci, const double *v, const int *arp,
+                               const int *aci, double *aw) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        for (int e = arp[u]; e < arp[u + 1]; ++e) {
+            int w = aci[e];
+            int lo = u < w ? u : w, hi = u < w ? w : u;
+            int e1 = find_col(ci, rp[lo], rp[lo + 1], hi);
+            int e2 = find_col(ci, rp[hi], rp[hi + 1], lo);
+            double a1 = e1 >= 0 ? fabs(v[e1]) : 0.0;
+            double a2 = e2 >= 0 ? fabs(v[e2]) : 0.0;
+            aw[e] = __dmul_rn(__dadd_rn(a1, a2), 0.5);
+        }
+    }
+}
+
+struct EKey {
+    double w;
+    uint64_t h;
+    int lo, hi;
+};
+
+__device__ __forceinline__ bool key_greater(const EKey &a, const EKey &b) {
+    if (a.w != b.w) return a.w > b.w;
+    if (a.h != b.h) return a.h > b.h;
+    if (a.lo != b.lo) return a.lo > b.lo;
+    return a.hi > b.hi;
+}
+
+__global__ void k_propose(int n, const int *arp, const int *aci, const double *aw, uint64_t seed,
+                          int *mate, int *prop, int *active) {
+    int cnt = 0;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        if (ld_volatile(mate + u) != -1) { prop[u] = -1; continue; }
+        int best = -1;
+        EKey bk{0.0, 0, 0, 0};
+        for (int e = arp[u]; e < arp[u + 1]; ++e) {
+            int v = aci[e];
+            double w = aw[e];
+            if (!(w > 0.0)) continue;
+            if (ld_volatile(mate + v) != -1) continue;
+            int lo = u < v ? u : v, hi = u < v ? v : u;
+            EKey k{w, mix64((((uint64_t)(uint32_t)lo) << 32 | (uint64_t)(uint32_t)hi) ^ seed), lo, hi};
+            if (best < 0 || key_greater(k, bk)) { best = v; bk = k; }
+        }
+        prop[u] = best;
+        if (best < 0) mate[u] = -2;      // no free neighbour left: stays a singleton
+        else ++cnt;
+    }
+    if (cnt) atomicAdd(active, cnt);
+}
+
+__global__ void k_accept(int n, int *mate, const int *prop) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        int v = prop[u];
+        if (v >= 0 && prop[v] == u) mate[u] = v;
+    }
+}
+
+__global__ void k_unmark_dead(int n, int *mate) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+        if (mate[u] < 0) mate[u] = -1;
+}
+
+int match_pass(const DCsr &A, const int *arp, const int *aci, int annz, uint64_t seed, int *mate,
+               cudaStream_t s) {
+    const int n = A.n;
+    DBuf<double> aw(annz > 0 ? annz : 1);
+    DBuf<int> prop(n), active(1);
+    k_edge_weights<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), arp, aci, aw.get());
+    CU_LAUNCH("k_edge_weights"); count_launch();
+    fill_int(mate, -1, n, s);
+    int *hactive = nullptr;
+    CU(cudaMallocHost(&hactive, sizeof(int)));
+    const int max_rounds = 100000;
+    int rounds = 0;
+    for (;;) {
+        if (rounds >= max_rounds) {
+            cudaFreeHost(hactive);
+            fail(8, "matching: handshake rounds exceeded the cap");
+        }
+        CU(cudaMemsetAsync(active.get(), 0, sizeof(int), s));
+        k_propose<<<grid_for(n, 256), 256, 0, s>>>(n, arp, aci, aw.get(), seed, mate, prop.get(), active.get());
+        CU_LAUNCH("k_propose"); count_launch();
+        k_accept<<<grid_for(n, 256), 256, 0, s>>>(n, mate, prop.get());
+        CU_LAUNCH("k_accept"); count_launch();
+        CU(cudaMemcpyAsync(hactive, active.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        ++rounds;
+        if (*hactive == 0) break;
+    }
+    cudaFreeHost(hactive);
+    k_unmark_dead<<<grid_for(n, 256), 256, 0, s>>>(n, mate);
+    CU_LAUNCH("k_unmark_dead"); count_launch();
+    return rounds;
+}
+
+// ------------------------------------------------------------------ aggregates
+__global__ void k_leader(int n, const int *mate, int *flag) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+        flag[u] = (mate[u] < 0 || u < mate[u]) ? 1 : 0;
+}
+__global__ void k_agg_from_ids(int n, const int *mate, const int *id, int *agg) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        int m = mate[u];
+        agg[u] = id[(m >= 0 && m < u) ? m : u];
+    }
+}
+
+int aggregates_from_mate(int n, const int *mate, int *agg, cudaStream_t s) {
+    DBuf<int> flag(n), id(n);
+    k_leader<<<grid_for(n, 256), 256, 0, s>>>(n, mate, flag.get());
+    CU_LAUNCH("k_leader"); count_launch();
+    int nc = 0;
+    exclusive_scan_int(flag.get(), id.get(), n, &nc, s);
+    k_agg_from_ids<<<grid_for(n, 256), 256, 0, s>>>(n, mate, id.get(), agg);
+    CU_LAUNCH("k_agg_from_ids"); count_launch();
+    CU(cudaStreamSynchronize(s));
+    return nc;
+}
+
+__global__ void k_int_to_key(const int *a, uint32_t *k, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) k[i] = (uint32_t)a[i];
+}
+
+void members_of(int n, int nc, const int *agg, DBuf<int> &ptr, DBuf<int> &idx, cudaStream_t s) {
+    DBuf<uint32_t> keys(n);
+    idx.alloc(n);
+    k_int_to_key<<<grid_for(n, 256), 256, 0, s>>>(agg, keys.get(), n);
+    CU_LAUNCH("k_int_to_key"); count_launch();
+    iota_int(idx.get(), n, s);
+    radix_sort_pairs(keys.get(), idx.get(), n, bits_for((uint32_t)nc), s);
+    segment_ptr(keys.get(), n, nc, ptr, s);
+    CU(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ Galerkin
+// Coarse row I gathers the rows of its members (ascending), each in stored
+// column order, maps columns through agg, sorts stably by coarse column and
+// sums each run in that order: the entrywise formula of Section 2 with the
+// summation order of a stable sort of A's entries by (agg[k], agg[l]).
+// Rows gathering at most GAL_CAP entries are handled by one thread; longer
+// rows (deep coarse levels) by one block that sorts (column, gather index)
+// keys in shared memory.
+constexpr int GAL_CAP = 128;
+constexpr int GAL_BIG = 4096;
+
+__device__ int gal_collect(int I, const int *rp, const int *ci, const double *v, const int *agg,
+                           const int *mptr, const int *midx, int *kJ, double *kv) {
+    int m = 0;
+    for (int t = mptr[I]; t < mptr[I + 1]; ++t) {
+        int row = midx[t];
+        for (int e = rp[row]; e < rp[row + 1]; ++e) {
+            int J = agg[ci[e]];
+            double x = v[e];
+            int p = m;                       // stable insertion: after equal keys
+            while (p > 0 && kJ[p - 1] > J) { kJ[p] = kJ[p - 1]; kv[p] = kv[p - 1]; --p; }
+            kJ[p] = J; kv[p] = x;
+            ++m;
+        }
+    }
+    return m;
+}
+
+__device__ __forceinline__ int gal_len(int I, const int *rp, const int *mptr, const int *midx) {
+    int m = 0;
+    for (int t = mptr[I]; t < mptr[I + 1]; ++t) m += rp[midx[t] + 1] - rp[midx[t]];
+    return m;
+}
+
+__global__ void k_gal_count(int nc, const int *rp, const int *ci, const double *v, const int *agg,
+                            const int *mptr, const int *midx, int *cnt, int *big, int *nbig) {
+    int kJ[GAL_CAP];
+    double kv[GAL_CAP];
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+        if (gal_len(I, rp, mptr, midx) > GAL_CAP) {
+            big[atomicAdd(nbig, 1)] = I;
+            cnt[I] = 0;
+            continue;
+        }
+        int m = gal_collect(I, rp, ci, v, agg, mptr, midx, kJ, kv);
+        int u = 0;
+        for (int t = 0; t < m; ++t) if (t == 0 || kJ[t] != kJ[t - 1]) ++u;
+        cnt[I] = u;
+    }
+}
+
+__global__ void k_gal_fill(int nc, const int *rp, const int *ci, const double *v, const int *agg,
+                           const int *mptr, const int *midx, const int *crp, int *cci, double *cv) {
+    int kJ[GAL_CAP];
+    double kv[GAL_CAP];
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+        if (gal_len(I, rp, mptr, midx) > GAL_CAP) continue;
+        int m = gal_collect(I, rp, ci, v, agg, mptr, midx, kJ, kv);
+        int out = crp[I] - 1;
+        double acc = 0.0;
+        for (int t = 0; t < m; ++t) {
+            if (t == 0 || kJ[t] != kJ[t - 1]) {
+                if (out >= crp[I]) cv[out] = acc;
+                ++out;
+                cci[out] = kJ[t];
+                acc = kv[t];
+            } else {
+                acc = __dadd_rn(acc, kv[t]);
+            }
+        }
+        if (m > 0) cv[out] = acc;
+    }
+}
+
+// One block per long row: keys (J << 32 | gather index) bitonic-sorted in
+// shared memory; values stay in gather order.  mode 0 counts, mode 1 fills.
+__global__ void __launch_bounds__(256) k_gal_big(const int *big, const int *rp, const int *ci, const double *v,
+                                                 const int *agg, const int *mptr, const int *midx, int *cnt,
+                                                 const int *crp, int *cci, double *cv, int mode, int *overflow) {
+    extern __shared__ unsigned char smem[];
+    uint64_t *key = reinterpret_cast<uint64_t *>(smem);
+    double *val = reinterpret_cast<double *>(smem + sizeof(uint64_t) * GAL_BIG);
+    __shared__ int m_s, P_s;
+    const int I = big[blockIdx.x];
+    if (threadIdx.x == 0) {
+        int m = gal_len(I, rp, mptr, midx);
+        m_s = m;
+        int P = 1;
+        while (P < m) P <<= 1;
+        P_s = P;
+        if (m > GAL_BIG) atomicExch(overflow, 1);
+    }
+    __syncthreads();
+    const int m = m_s, P = P_s;
+    if (m > GAL_BIG) return;
+    // gather: the k-th entry in (member ascending, column ascending) order
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int t = mptr[I]; t < mptr[I + 1]; ++t) {
+            int row = midx[t];
+            for (int e = rp[row]; e < rp[row + 1]; ++e, ++k) {
+                key[k] = ((uint64_t)(uint32_t)agg[ci[e]] << 32) | (uint32_t)k;
+                val[k] = v[e];
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = m + threadIdx.x; k < P; k += blockDim.x) key[k] = ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                int partner = t ^ stride;
+                if (partner > t) {
+                    bool up = (t & size) == 0;
+                    uint64_t a = key[t], b = key[partner];
+                    if ((a > b) == up) { key[t] = b; key[partner] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        int out = mode ? crp[I] - 1 : -1, u = 0;
+        double acc = 0.0;
+        for (int t = 0; t < m; ++t) {
+            const int J = (int)(key[t] >> 32);
+            const double x = val[(uint32_t)key[t]];
+            if (t == 0 || J != (int)(key[t - 1] >> 32)) {
+                ++u;
+                if (mode) {
+                    if (out >= crp[I]) cv[out] = acc;
+                    ++out;
+                    cci[out] = J;
+                }
+                acc = x;
+            } else {
+                acc = __dadd_rn(acc, x);
+            }
+        }
+        if (mode) { if (m > 0) cv[out] = acc; }
+        else cnt[I] = u;
+    }
+}
+
+void galerkin(const DCsr &A, int nc, const int *agg, const int *mptr, const int *midx, DCsr &C,
+              cudaStream_t s) {
+    DBuf<int> cnt(nc + 1), big(nc > 0 ? nc : 1), flags(2);
+    CU(cudaMemsetAsync(flags.get(), 0, 2 * sizeof(int), s));
+    fill_int(cnt.get(), 0, nc + 1, s);
+    k_gal_count<<<grid_for(nc, 128), 128, 0, s>>>(nc, A.rp.get(), A.ci.get(), A.v.get(), agg, mptr, midx,
+                                                  cnt.get(), big.get(), flags.get());
+    CU_LAUNCH("k_gal_count"); count_launch();
+    const int nbig = read_int(flags.get(), s);
+    const size_t smem = (sizeof(uint64_t) + sizeof(double)) * GAL_BIG;
+    if (nbig > 0) {
+        CU(cudaFuncSetAttribute(k_gal_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_gal_big<<<nbig, 256, smem, s>>>(big.get(), A.rp.get(), A.ci.get(), A.v.get(), agg, mptr, midx,
+                                          cnt.get(), nullptr, nullptr, nullptr, 0, flags.get() + 1);
+        CU_LAUNCH("k_gal_big"); count_launch();
+        if (read_int(flags.get() + 1, s)) fail(8, "Galerkin: a coarse row gathers more than 4096 fine entries");
+    }
+    C.n = nc;
+    C.rp.alloc(nc + 1);
+    exclusive_scan_int(cnt.get(), C.rp.get(), nc + 1, &C.nnz, s);
+    C.ci.alloc(C.nnz > 0 ? C.nnz : 1);
+    C.v.alloc(C.nnz > 0 ? C.nnz : 1);
+    k_gal_fill<<<grid_for(nc, 128), 128, 0, s>>>(nc, A.rp.get(), A.ci.get(), A.v.get(), agg, mptr, midx,
+                                                 C.rp.get(), C.ci.get(), C.v.get());
+    CU_LAUNCH("k_gal_fill"); count_launch();
+    if (nbig > 0) {
+        k_gal_big<<<nbig, 256, smem, s>>>(big.get(), A.rp.get(), A.ci.get(), A.v.get(), agg, mptr, midx,
+                                          cnt.get(), C.rp.get(), C.ci.get(), C.v.get(), 1, flags.get() + 1);
+        CU_LAUNCH("k_gal_big"); count_launch();
+    }
+    CU(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ colouring
+// Jones-Plassmann rounds: a vertex whose higher-priority neighbours are all
+// coloured takes the smallest colour none of them uses.  This reproduces the
+// sequential greedy colouring in decreasing priority order.
+constexpr int MAX_COLORS = 256;
+__device__ __forceinline__ bool prio_higher(int a, int b, int mode, uint64_t seed) {
+    if (mode == 1) return a < b;                        // first fit: lower index first
+    const uint64_t salt = 0x9e3779b97f4a7c15ull;
+    uint64_t ha = mix64((uint64_t)(uint32_t)a ^ (seed + salt));
+    uint64_t hb = mix64((uint64_t)(uint32_t)b ^ (seed + salt));
+    if (ha != hb) return ha > hb;
+    return a > b;
+}
+
+__global__ void k_jp_round(int n, const int *arp, const int *aci, int mode, uint64_t seed, int *color,
+                           int *remaining, int *overflow) {
+    int rem = 0;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        if (ld_volatile(color + u) >= 0) continue;
+        uint64_t mask[MAX_COLORS / 64] = {0, 0, 0, 0};
+        bool ready = true;
+        for (int e = arp[u]; e < arp[u + 1]; ++e) {
+            int v = aci[e];
+            if (!prio_higher(v, u, mode, seed)) continue;
+            int cv = ld_volatile(color + v);
+            if (cv < 0) { ready = false; break; }
+            if (cv < MAX_COLORS) mask[cv >> 6] |= 1ull << (cv & 63);
+        }
+        if (!ready) { ++rem; continue; }
+        int c = 0;
+        while (c < MAX_COLORS && (mask[c >> 6] >> (c & 63)) & 1ull) ++c;
+        if (c >= MAX_COLORS) { atomicExch(overflow, 1); c = MAX_COLORS - 1; }
+        *(volatile int *)(color + u) = c;
+    }
+    if (rem) atomicAdd(remaining, rem);
+}
+
+__global__ void k_max_int(const int *a, int n, int *out) {
+    int m = -1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = max(m, a[i]);
+    for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+static int max_of(const int *a, int n, cudaStream_t s) {
+    DBuf<int> out(1);
+    fill_int(out.get(), -1, 1, s);
+    k_max_int<<<grid_for(n, 256), 256, 0, s>>>(a, n, out.get());
+    CU_LAUNCH("k_max_int"); count_launch();
+    return read_int(out.get(), s);
+}
+
+int color_jp(int n, const int *arp, const int *aci, int mode, uint64_t seed, int *color, cudaStream_t s) {
+    DBuf<int> rem(1), overflow(1);
+    fill_int(color, -1, n, s);
+    CU(cudaMemsetAsync(overflow.get(), 0, sizeof(int), s));
+    int *h = nullptr;
+    CU(cudaMallocHost(&h, sizeof(int)));
+    const int max_rounds = 1000000;
+    int rounds = 0;
+    for (;;) {
+        if (rounds >= max_rounds) { cudaFreeHost(h); fail(8, "colouring: rounds exceeded the cap"); }
+        CU(cudaMemsetAsync(rem.get(), 0, sizeof(int), s));
+        k_jp_round<<<grid_for(n, 256), 256, 0, s>>>(n, arp, aci, mode, seed, color, rem.get(), overflow.get());
+        CU_LAUNCH("k_jp_round"); count_launch();
+        CU(cudaMemcpyAsync(h, rem.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        ++rounds;
+        if (*h == 0) break;
+    }
+    cudaFreeHost(h);
+    if (read_int(overflow.get(), s)) fail(8, "colouring: more than 256 colours");
+    return max_of(color, n, s) + 1;
+}
+
+// ------------------------------------------------------------------ elimination order
+__global__ void k_invert_perm(const int *perm, int *pos, int n) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) pos[perm[k]] = k;
+}
+
+void elimination_positions(int n, const int *label, int nlabels, int *pos, cudaStream_t s) {
+    DBuf<uint32_t> keys(n);
+    DBuf<int> perm(n);
+    k_int_to_key<<<grid_for(n, 256), 256, 0, s>>>(label, keys.get(), n);
+    CU_LAUNCH("k_int_to_key"); count_launch();
+    iota_int(perm.get(), n, s);
+    if (nlabels > 1) radix_sort_pairs(keys.get(), perm.get(), n, bits_for((uint32_t)nlabels), s);
+    k_invert_perm<<<grid_for(n, 256), 256, 0, s>>>(perm.get(), pos, n);
+    CU_LAUNCH("k_invert_perm"); count_launch();
+    CU(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ sweep schedules
+// Longest-path depth in the dependency graph of the forward (pos[j] <
+// pos[i]) or backward (pos[j] > pos[i]) solve, by monotone relaxation.
+__global__ void k_level_relax(int n, const int *rp, const int *ci, const int *pos, int *lev, int fwd,
+                              int *changed) {
+    int ch = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int pi = pos[i], m = -1;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            int j = ci[e];
+            int pj = pos[j];
+            if (fwd ? (pj < pi) : (pj > pi)) m = max(m, ld_volatile(lev + j));
+        }
+        int nl = m + 1;
+        if (nl > ld_volatile(lev + i)) { *(volatile int *)(lev + i) = nl; ch = 1; }
+    }
+    if (ch) atomicExch(changed, 1);
+}
+
+static int schedule_levels(const DCsr &A, const int *pos, int fwd, int *lev, cudaStream_t s) {
+    DBuf<int> changed(1);
+    fill_int(lev, 0, A.n, s);
+    int *h = nullptr;
+    CU(cudaMallocHost(&h, sizeof(int)));
+    int it = 0;
+    for (;; ++it) {
+        if (it > A.n + 2) { cudaFreeHost(h); fail(8, "sweep schedule did not settle"); }
+        CU(cudaMemsetAsync(changed.get(), 0, sizeof(int), s));
+        k_level_relax<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp.get(), A.ci.get(), pos, lev, fwd, changed.get());
+        CU_LAUNCH("k_level_relax"); count_launch();
+        CU(cudaMemcpyAsync(h, changed.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (!*h) break;
+    }
+    cudaFreeHost(h);
+    return max_of(lev, A.n, s) + 1;
+}
+
+__global__ void k_sweep_count(int n, const int *rows, const int *rp, const int *ci, const int *pos, int fwd,
+                              int *cnt) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int i = rows[k], pi = pos[i], m = 0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            int pj = pos[ci[e]];
+            if (fwd ? (pj < pi) : (pj > pi)) ++m;
+        }
+        cnt[k] = m;
+    }
+}
+
+__global__ void k_sweep_fill(int n, const int *rows, const int *rp, const int *ci, const double *lu,
+                             const int *pos, int fwd, const int *srp, int *sci, double *sv, double *diag) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int i = rows[k], pi = pos[i], m = srp[k];
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            int j = ci[e];
+            int pj = pos[j];
+            if (fwd ? (pj < pi) : (pj > pi)) { sci[m] = j; sv[m] = lu[e]; ++m; }
+            else if (j == i && diag) diag[k] = lu[e];
+        }
+    }
+}
+
+static void build_sweep(const DCsr &A, const int *pos, const double *lu, int fwd, int want_diag, const int *lev,
+                        int nlev, Sweep &S, cudaStream_t s) {
+    const int n = A.n;
+    DBuf<uint32_t> keys(n);
+    S.rows.alloc(n);
+    k_int_to_key<<<grid_for(n, 256), 256, 0, s>>>(lev, keys.get(), n);
+    CU_LAUNCH("k_int_to_key"); count_launch();
+    iota_int(S.rows.get(), n, s);
+    if (nlev > 1) radix_sort_pairs(keys.get(), S.rows.get(), n, bits_for((uint32_t)nlev), s);
+    DBuf<int> lp;
+    segment_ptr(keys.get(), n, nlev, lp, s);
+    S.nlev = nlev;
+    S.lev_ptr.resize(nlev + 1);
+    CU(cudaMemcpyAsync(S.lev_ptr.data(), lp.get(), sizeof(int) * (nlev + 1), cudaMemcpyDeviceToHost, s));
+    DBuf<int> cnt(n + 1);
+    fill_int(cnt.get(), 0, n + 1, s);
+    k_sweep_count<<<grid_for(n, 256), 256, 0, s>>>(n, S.rows.get(), A.rp.get(), A.ci.get(), pos, fwd, cnt.get());
+    CU_LAUNCH("k_sweep_count"); count_launch();
+    S.rp.alloc(n + 1);
+    int nnzf = 0;
+    exclusive_scan_int(cnt.get(), S.rp.get(), n + 1, &nnzf, s);
+    S.ci.alloc(nnzf > 0 ? nnzf : 1);
+    S.v64.alloc(nnzf > 0 ? nnzf : 1);
+    if (want_diag) S.d64.alloc(n);
+    k_sweep_fill<<<grid_for(n, 256), 256, 0, s>>>(n, S.rows.get(), A.rp.get(), A.ci.get(), lu, pos, fwd,
+                                                  S.rp.get(), S.ci.get(), S.v64.get(), want_diag ? S.d64.get() : nullptr);
+    CU_LAUNCH("k_sweep_fill"); count_launch();
+    CU(cudaStreamSynchronize(s));
+    S.maxlev = 0;
+    for (int l = 0; l < nlev; ++l) S.maxlev = std::max(S.maxlev, S.lev_ptr[l + 1] - S.lev_ptr[l]);
+}
+
+// ------------------------------------------------------------------ ILU(0)
+// IKJ ILU(0) on the pattern of A in the elimination order pos (Algorithm 1:
+// S = L0 U0 = ILU0(A)): for each stored k of row i with pos(k) < pos(i), in
+// increasing pos(k): a_ik /= a_kk, then a_ij -= a_ik a_kj for every stored
+// (k, j) with pos(j) > pos(k) whose (i, j) is stored.  Rows of one schedule
+// level only read rows of earlier levels, so a level runs in parallel.
+constexpr int ILU_CAP = 256;
+
+__global__ void k_ilu_rows(const int *rows, int count, const int *rp, const int *ci, const int *pos,
+                           const int *dpos, double *lu, int *breakdown, int *overflow) {
+    int lp[ILU_CAP], le[ILU_CAP];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        const int i = rows[t], pi = pos[i], rb = rp[i], re = rp[i + 1];
+        int nl = 0;
+        bool over = false;
+        for (int e = rb; e < re; ++e) {
+            int p = pos[ci[e]];
+            if (p < pi) {
+                if (nl >= ILU_CAP) { over = true; break; }
+                int q = nl++;
+                while (q > 0 && lp[q - 1] > p) { lp[q] = lp[q - 1]; le[q] = le[q - 1]; --q; }
+                lp[q] = p; le[q] = e;
+            }
+        }
+        if (over) { atomicExch(overflow, 1); continue; }
+        for (int a = 0; a < nl; ++a) {
+            const int eik = le[a], k = ci[eik];
+            const int pk = lp[a];
+            const double lik = __ddiv_rn(lu[eik], lu[dpos[k]]);
+            lu[eik] = lik;
+            int p = rb;                              // walk row i and row k by column
+            for (int ekj = rp[k]; ekj < rp[k + 1]; ++ekj) {
+                const int j = ci[ekj];
+                if (pos[j] <= pk) continue;
+                while (p < re && ci[p] < j) ++p;
+                if (p < re && ci[p] == j) lu[p] = __dsub_rn(lu[p], __dmul_rn(lik, lu[ekj]));
+            }
+        }
+        double piv = lu[dpos[i]];
+        if (piv == 0.0 || !isfinite(piv)) atomicExch(breakdown, 1);
+    }
+}
+
+__global__ void k_diag_pos(int n, const int *rp, const int *ci, int *dpos) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dpos[i] = find_col(ci, rp[i], rp[i + 1], i);
+}
+
+void ilu0_factor(const DCsr &A, const int *pos, DBuf<double> &lu, Sweep &fwd, Sweep &bwd, cudaStream_t s) {
+    const int n = A.n;
+    DBuf<int> levf(n), levb(n), dpos(n), flags(2);
+    const int nf = schedule_levels(A, pos, 1, levf.get(), s);
+    const int nb = schedule_levels(A, pos, 0, levb.get(), s);
+    lu.alloc(A.nnz > 0 ? A.nnz : 1);
+    CU(cudaMemcpyAsync(lu.get(), A.v.get(), sizeof(double) * A.nnz, cudaMemcpyDeviceToDevice, s));
+    k_diag_pos<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), dpos.get());
+    CU_LAUNCH("k_diag_pos"); count_launch();
+    CU(cudaMemsetAsync(flags.get(), 0, 2 * sizeof(int), s));
+    // forward schedule rows (needed to run the factorisation level by level)
+    Sweep tmp;
+    {
+        DBuf<uint32_t> keys(n);
+        tmp.rows.alloc(n);
+        k_int_to_key<<<grid_for(n, 256), 256, 0, s>>>(levf.get(), keys.get(), n);
+        CU_LAUNCH("k_int_to_key"); count_launch();
+        iota_int(tmp.rows.get(), n, s);
+        if (nf > 1) radix_sort_pairs(keys.get(), tmp.rows.get(), n, bits_for((uint32_t)nf), s);
+        DBuf<int> lp;
+        segment_ptr(keys.get(), n, nf, lp, s);
+        tmp.lev_ptr.resize(nf + 1);
+        CU(cudaMemcpyAsync(tmp.lev_ptr.data(), lp.get(), sizeof(int) * (nf + 1), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    for (int l = 0; l < nf; ++l) {
+        const int b = tmp.lev_ptr[l], cnt = tmp.lev_ptr[l + 1] - b;
+        if (cnt <= 0) continue;
+        k_ilu_rows<<<grid_for(cnt, 128), 128, 0, s>>>(tmp.rows.get() + b, cnt, A.rp.get(), A.ci.get(), pos,
+                                                      dpos.get(), lu.get(), flags.get(), flags.get() + 1);
+        CU_LAUNCH("k_ilu_rows"); count_launch();
+    }
+    int hf[2];
+    CU(cudaMemcpyAsync(hf, flags.get(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (hf[1]) fail(8, "ILU(0): a row has more than 256 entries before the diagonal");
+    if (hf[0]) fail(5, "ILU(0): zero or non-finite pivot");
+    build_sweep(A, pos, lu.get(), 1, 0, levf.get(), nf, fwd, s);
+    build_sweep(A, pos, lu.get(), 0, 1, levb.get(), nb, bwd, s);
+}
+
+__global__ void k_gather_vals(const double *src, const int *idx, double *dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];
+}
+
+// Sweeps of (L U)^T = U^T L^T on the transposed layout: row j of the
+// transpose holds u_ij for pos(i) < pos(j) (forward solve U^T w = r with
+// division by u_jj) and l_ij for pos(i) > pos(j) (backward solve L^T t = w,
+// unit diagonal).
+void build_transposed_sweeps(const DCsr &A, const int *pos, const double *lu, Sweep &fwdT, Sweep &bwdT,
+                             cudaStream_t s) {
+    DCsr T;
+    DBuf<int> tsrc;
+    csr_transpose(A.n, A.nnz, A.rp.get(), A.ci.get(), T.rp, T.ci, tsrc, s);
+    T.n = A.n;
+    T.nnz = A.nnz;
+    T.v.alloc(A.nnz > 0 ? A.nnz : 1);
+    if (A.nnz) {
+        k_gather_vals<<<grid_for(A.nnz, 256), 256, 0, s>>>(lu, tsrc.get(), T.v.get(), A.nnz);
+        CU_LAUNCH("k_gather_vals"); count_launch();
+    }
+    DBuf<int> levf(A.n), levb(A.n);
+    const int nf = schedule_levels(T, pos, 1, levf.get(), s);
+    const int nb = schedule_levels(T, pos, 0, levb.get(), s);
+    build_sweep(T, pos, T.v.get(), 1, 1, levf.get(), nf, fwdT, s);
+    build_sweep(T, pos, T.v.get(), 0, 0, levb.get(), nb, bwdT, s);
+}
+
+// ------------------------------------------------------------------ dense inverse
+// Gauss-Jordan elimination with partial pivoting on [A | I] (FP64).  The
+// pivot of column k is the first row of largest magnitude at or below k.
+__global__ void k_dense_from_csr(int n, const int *rp, const int *ci, const double *v, double *M) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double *row = M + (size_t)i * 2 * n;
+        for (int j = 0; j < 2 * n; ++j) row[j] = (j == n + i) ? 1.0 : 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) row[ci[e]] = v[e];
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *M, double *f, int *breakdown) {
+    __shared__ double bv[32];
+    __shared__ int bi[32];
+    __shared__ int piv;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double best = -1.0;
+    int bidx = n;
+    for (int i = k + tid; i < n; i += blockDim.x) {
+        double a = fabs(M[(size_t)i * 2 * n + k]);
+        if (a > best || (a == best && i < bidx)) { best = a; bidx = i; }
+    }
+    for (int off = 16; off; off >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if (lane == 0) { bv[warp] = best; bi[warp] = bidx; }
+    __syncthreads();
+    if (tid == 0) {
+        double b = -1.0;
+        int p = n;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w)
+            if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
+        if (!(b > 0.0) || !isfinite(b)) { atomicExch(breakdown, 1); p = k; }
+        piv = p;
+    }
+    __syncthreads();
+    const int p = piv;
+    double *rk = M + (size_t)k * 2 * n, *rpiv = M + (size_t)p * 2 * n;
+    if (p != k)
+        for (int j = tid; j < 2 * n; j += blockDim.x) { double t = rk[j]; rk[j] = rpiv[j]; rpiv[j] = t; }
+    __syncthreads();
+    const double d = rk[k];
+    __syncthreads();
+    for (int j = tid; j < 2 * n; j += blockDim.x) rk[j] = rk[j] / d;
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : M[(size_t)i * 2 * n + k];
+}
+
+__global__ void k_gj_elim(int n, int k, double *M, const double *f) {
+    const size_t total = (size_t)n * 2 * n;
+    const double *rk = M + (size_t)k * 2 * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / (2 * n)), j = (int)(t % (2 * n));
+        if (i == k) continue;
+        const double fi = f[i];
+        if (fi != 0.0) M[t] = M[t] - fi * rk[j];
+    }
+}
+
+__global__ void k_extract_inverse(int n, const double *M, double *inv) {
+    const size_t total = (size_t)n * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        inv[t] = M[(size_t)i * 2 * n + n + j];
+    }
+}
+
+void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
+    const int n = A.n;
+    DBuf<double> M((size_t)n * 2 * n), f(n);
+    DBuf<int> bd(1);
+    CU(cudaMemsetAsync(bd.get(), 0, sizeof(int), s));
+    k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), M.get());
+    CU_LAUNCH("k_dense_from_csr"); count_launch();
+    const int eg = grid_for((size_t)n * 2 * n, 256);
+    for (int k = 0; k < n; ++k) {
+        k_gj_pivot<<<1, 1024, 0, s>>>(n, k, M.get(), f.get(), bd.get());
+        k_gj_elim<<<eg, 256, 0, s>>>(n, k, M.get(), f.get());
+        count_launch(2);
+    }
+    CU_LAUNCH("k_gj_*");
+    inv.alloc((size_t)n * n);
+    k_extract_inverse<<<grid_for((size_t)n * n, 256), 256, 0, s>>>(n, M.get(), inv.get());
+    CU_LAUNCH("k_extract_inverse"); count_launch();
+    if (read_int(bd.get(), s)) fail(5, "dense solve of the last level: singular matrix");
+}
+
+// ------------------------------------------------------------------ casts
+__global__ void k_cast32(const double *in, float *out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __double2float_rn(in[i]);
+}
+__global__ void k_cast16(const double *in, __nv_bfloat16 *out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __double2bfloat16(in[i]);
+}
+void cast_f64_f32(const double *in, float *out, size_t n, cudaStream_t s) {
+    if (!n) return;
+    k_cast32<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    CU_LAUNCH("k_cast32"); count_launch();
+}
+void cast_f64_bf16(const double *in, __nv_bfloat16 *out, size_t n, cudaStream_t s) {
+    if (!n) return;
+    k_cast16<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    CU_LAUNCH("k_cast16"); count_launch();
+}
+
+// ------------------------------------------------------------------ FV assembly (eq. (2))
+struct FvGrid {
+    int dim, nx, ny, nz;
+    double hd2, hd;
+};
+
+// Face q in W, E, S, N, B, T order: neighbour, kind (0 interior, 1
+// Dirichlet, 2 Neumann), conductivities, outward flux.
+__device__ __forceinline__ void fv_face(const FvGrid &g, int i, int j, int k, long P, int q,
+                                        const double *kx, const double *ky, const double *kz,
+                                        const double *fx, const double *fy, const double *fz,
+                                        long &nb, int &kind, double &kP, double &kN, double &F) {
+    const long sxy = (long)g.nx * g.ny;
+    switch (q) {
+    case 0: nb = P - 1; kind = (i == 0) ? 2 : 0; kP = kx[P]; kN = (i == 0) ? 0.0 : kx[P - 1];
+        F = -fx[i + (long)(g.nx + 1) * (j + (long)g.ny * k)]; break;
+    case 1: nb = P + 1; kind = (i == g.nx - 1) ? 2 : 0; kP = kx[P]; kN = (i == g.nx - 1) ? 0.0 : kx[P + 1];
+        F = fx[(i + 1) + (long)(g.nx + 1) * (j + (long)g.ny * k)]; break;
+    case 2: nb = P - g.nx; kind = (j == 0) ? 1 : 0; kP = ky[P]; kN = (j == 0) ? 0.0 : ky[P - g.nx];
+        F = -fy[i + (long)g.nx * (j + (long)(g.ny + 1) * k)]; break;
+    case 3: nb = P + g.nx; kind = (j == g.ny - 1) ? 1 : 0; kP = ky[P]; kN = (j == g.ny - 1) ? 0.0 : ky[P + g.nx];
+        F = fy[i + (long)g.nx * ((j + 1) + (long)(g.ny + 1) * k)]; break;
+    case 4: nb = P - sxy; kind = (k == 0) ? 2 : 0; kP = kz[P]; kN = (k == 0) ? 0.0 : kz[P - sxy];
+        F = -fz[i + (long)g.nx * (j + (long)g.ny * k)]; break;
+    default: nb = P + sxy; kind = (k == g.nz - 1) ? 2 : 0; kP = kz[P]; kN = (k == g.nz - 1) ? 0.0 : kz[P + sxy];
+        F = fz[i + (long)g.nx * (j + (long)g.ny * (k + 1))]; break;
+    }
+}
+
+__device__ __forceinline__ double harmonic_T(double hd2, double kP, double kN) {
+    return __dmul_rn(hd2, __ddiv_rn(__dmul_rn(__dmul_rn(2.0, kP), kN), __dadd_rn(kP, kN)));
+}
+
+__global__ void k_fv_count(FvGrid g, int *cnt) {
+    const long N = (long)g.nx * g.ny * g.nz;
+    for (long P = blockIdx.x * (long)blockDim.x + threadIdx.x; P < N; P += (long)gridDim.x * blockDim.x) {
+        int i = (int)(P % g.nx), j = (int)((P / g.nx) % g.ny), k = (int)(P / ((long)g.nx * g.ny));
+        int m = 1;
+        m += (i > 0) + (i < g.nx - 1) + (j > 0) + (j < g.ny - 1);
+        if (g.dim == 3) m += (k > 0) + (k < g.nz - 1);
+        cnt[P] = m;
+    }
+}
+
+__global__ void k_fv_fill(FvGrid g, const double *kx, const double *ky, const double *kz, const double *fx,
+                          const double *fy, const double *fz, const double *f, const int *rp32, int64_t *rp,
+                          int *ci, double *v, double *b) {
+    const long N = (long)g.nx * g.ny * g.nz;
+    for (long P = blockIdx.x * (long)blockDim.x + threadIdx.x; P < N; P += (long)gridDim.x * blockDim.x) {
+        int i = (int)(P % g.nx), j = (int)((P / g.nx) % g.ny), k = (int)(P / ((long)g.nx * g.ny));
+        const int nf = g.dim == 3 ? 6 : 4;
+        long nbv[6];
+        int kind[6];
+        double off[6];
+        double diag = 0.0;
+        for (int q = 0; q < nf; ++q) {
+            double kP, kN, F;
+            fv_face(g, i, j, k, P, q, kx, ky, kz, fx, fy, fz, nbv[q], kind[q], kP, kN, F);
+            off[q] = 0.0;
+            if (kind[q] == 0) {
+                double T = harmonic_T(g.hd2, kP, kN);
+                diag = __dadd_rn(diag, T);
+                if (F > 0.0) diag = __dadd_rn(diag, F);
+                off[q] = -T;
+                if (F < 0.0) off[q] = __dadd_rn(off[q], F);
+            } else if (kind[q] == 1) {
+                double T = __dmul_rn(g.hd2, __dmul_rn(2.0, kP));
+                diag = __dadd_rn(diag, T);
+                if (F > 0.0) diag = __dadd_rn(diag, F);
+            } else {
+                diag = __dadd_rn(diag, F);
+            }
+        }
+        const int ord3[7] = {4, 2, 0, -1, 1, 3, 5};
+        const int ord2[5] = {2, 0, -1, 1, 3};
+        const int *ord = g.dim == 3 ? ord3 : ord2;
+        const int nord = g.dim == 3 ? 7 : 5;
+        int m = rp32[P];
+        for (int t = 0; t < nord; ++t) {
+            int q = ord[t];
+            if (q < 0) { ci[m] = (int)P; v[m] = diag; ++m; }
+            else if (kind[q] == 0) { ci[m] = (int)nbv[q]; v[m] = off[q]; ++m; }
+        }
+        rp[P] = rp32[P];
+        if (P == N - 1) rp[N] = rp32[N];
+        b[P] = __dmul_rn(f[P], g.hd);
+    }
+}
+
+int64_t fv_assemble(int dim, int nx, int ny, int nz, const double *kx, const double *ky, const double *kz,
+                    const double *fx, const double *fy, const double *fz, const double *f, int64_t *rp, int *ci,
+                    double *v, double *b, cudaStream_t s) {
+    FvGrid g;
+    g.dim = dim; g.nx = nx; g.ny = ny; g.nz = nz;
+    const double h = 1.0 / (double)nx;
+    g.hd2 = dim == 2 ? 1.0 : h;
+    g.hd = dim == 2 ? h * h : h * h * h;
+    const long N = (long)nx * ny * nz;
+    DBuf<int> cnt(N + 1), rp32(N + 1);
+    fill_int(cnt.get(), 0, (int)(N + 1), s);
+    k_fv_count<<<grid_for(N, 256), 256, 0, s>>>(g, cnt.get());
+    CU_LAUNCH("k_fv_count"); count_launch();
+    int nnz = 0;
+    exclusive_scan_int(cnt.get(), rp32.get(), (int)(N + 1), &nnz, s);
+    k_fv_fill<<<grid_for(N, 256), 256, 0, s>>>(g, kx, ky, kz, fx, fy, fz, f, rp32.get(), rp, ci, v, b);
+    CU_LAUNCH("k_fv_fill"); count_launch();
+    CU(cudaStreamSynchronize(s));
+    return nnz;
+}
+
+__global__ void k_fv_grad(FvGrid g, const double *kx, const double *ky, const double *kz, const double *lam,
+                          const double *x, double *gx, double *gy, double *gz) {
+    const long N = (long)g.nx * g.ny * g.nz;
+    const long sxy = (long)g.nx * g.ny;
+    for (long P = blockIdx.x * (long)blockDim.x + threadIdx.x; P < N; P += (long)gridDim.x * blockDim.x) {
+        int c[3] = {(int)(P % g.nx), (int)((P / g.nx) % g.ny), (int)(P / sxy)};
+        int dims[3] = {g.nx, g.ny, g.nz};
+        long stride[3] = {1, g.nx, sxy};
+        for (int axis = 0; axis < g.dim; ++axis) {
+            const double *kk = axis == 0 ? kx : (axis == 1 ? ky : kz);
+            double acc = 0.0;
+            for (int side = 0; side < 2; ++side) {
+                bool bnd = side == 0 ? (c[axis] == 0) : (c[axis] == dims[axis] - 1);
+                if (bnd) {
+                    if (axis == 1) {
+                        double T = __dmul_rn(g.hd2, __dmul_rn(2.0, kk[P]));
+                        double dLdT = -lam[P] * x[P];
+                        acc = __dadd_rn(acc, __dmul_rn(dLdT, T));
+                    }
+                    continue;
+                }
+                long Q = side == 0 ? P - stride[axis] : P + stride[axis];
+                double kP = kk[P], kN = kk[Q];
+                double T = harmonic_T(g.hd2, kP, kN);
+                double dLdT = __dmul_rn(-__dsub_rn(lam[P], lam[Q]), __dsub_rn(x[P], x[Q]));
+                acc = __dadd_rn(acc, __dmul_rn(dLdT, __ddiv_rn(__dmul_rn(T, kN), __dadd_rn(kP, kN))));
+            }
+            double *gg = axis == 0 ? gx : (axis == 1 ? gy : gz);
+            gg[P] = acc;
+        }
+    }
+}
+
+void fv_grad_logk(int dim, int nx, int ny, int nz, const double *kx, const double *ky, const double *kz,
+                  const double *lam, const double *x, double *gx, double *gy, double *gz, cudaStream_t s) {
+    FvGrid g;
+    g.dim = dim; g.nx = nx; g.ny = ny; g.nz = nz;
+    const double h = 1.0 / (double)nx;
+    g.hd2 = dim == 2 ? 1.0 : h;
+    g.hd = dim == 2 ? h * h : h * h * h;
+    const long N = (long)nx * ny * nz;
+    k_fv_grad<<<grid_for(N, 256), 256, 0, s>>>(g, kx, ky, kz, lam, x, gx, gy, gz);
+    CU_LAUNCH("k_fv_grad"); count_launch();
+}
+
+}  // namespace amg

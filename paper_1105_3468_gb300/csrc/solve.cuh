@@ -1,0 +1,75 @@
+// solve.cuh -- declarations of the solve-phase kernels' host launchers and
+// the device-resident FGMRES state.
+#pragma once
+
+#include "internal.cuh"
+
+namespace amg {
+
+// Largest restart length supported by the fused multi-dot kernels.
+constexpr int KMAX1 = 32;
+
+// FGMRES scalars, resident in device memory and updated by single-thread
+// kernels (Givens, back substitution) so that the inner loop needs no host
+// round trip except the stop flag.
+struct FgState {
+    int m, maxit, total, hist_len, hist_cap, jdone, stop, status;
+    double tol, bnorm, inv_hn, pad;
+    double H[(KMAX1 + 1) * KMAX1];
+    double cs[KMAX1], sn[KMAX1], s[KMAX1 + 1], y[KMAX1];
+    double h1[KMAX1 + 1], h2[KMAX1 + 1], nrm2[2];
+    double *hist;
+};
+
+// Matrix view for a level in value type V.
+template <typename V>
+struct LevelMats {
+    int n, nnz;
+    const int *rp, *ci;
+    const V *v;
+};
+
+// Sweep view in vector type T and value type V.
+template <typename T, typename V>
+struct SweepView {
+    int nlev;
+    const int *lev_ptr;   // host
+    const int *rows, *rp, *ci;
+    const V *v;
+    const T *d;           // diagonal per schedule position (or nullptr)
+};
+
+void spmv_f64(int n, int nnz, const int *rp, const int *ci, const double *v, const double *x, double *y, cudaStream_t s);
+void spmv_f64_xf32(int n, int nnz, const int *rp, const int *ci, const double *v, const float *x, double *y, cudaStream_t s);
+void residual_f64(int n, int nnz, const int *rp, const int *ci, const double *v, const double *x, const double *b,
+                  double *r, cudaStream_t s);
+
+template <typename T, typename V>
+void level_residual(const LevelMats<V> &M, const T *x, const T *b, T *r, cudaStream_t s);
+template <typename T, typename V>
+void sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag, cudaStream_t s);
+template <typename T>
+void restrict_to(int nc, const int *mptr, const int *midx, const T *r, T *h, cudaStream_t s);
+template <typename T, typename Q>
+void prolong(int n, const int *agg, const T *t, const T *g, Q *q, int mode, cudaStream_t s);
+template <typename T>
+void vec_acc(size_t n, const T *in, T *out, int mode, cudaStream_t s);
+void convert_f64_f32(size_t n, const double *in, float *out, cudaStream_t s);
+void convert_f32_f64(size_t n, const float *in, double *out, cudaStream_t s);
+template <typename T>
+void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, cudaStream_t s);
+
+void mdot(size_t n, int K, const double *w, const double *V, size_t ldv, double *partials, unsigned int *ticket,
+          double *h, cudaStream_t s);
+void cgs_update(size_t n, int K, const double *hin, double *w, const double *V, size_t ldv, int want_dots,
+                double *partials, unsigned int *ticket, double *hout, cudaStream_t s);
+void norm2(size_t n, const double *v, double *partials, unsigned int *ticket, double *out, cudaStream_t s);
+void givens(FgState *st, int j, cudaStream_t s);
+void scale_next(size_t n, const double *w, double *vout, const FgState *st, cudaStream_t s);
+void backsolve(FgState *st, cudaStream_t s);
+template <typename ZT>
+void update_x(size_t n, const FgState *st, const ZT *Z, size_t ldz, double *x, cudaStream_t s);
+void restart_scale(size_t n, const double *r, double *v0, FgState *st, cudaStream_t s);
+int reduce_grid();
+
+}  // namespace amg

@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (the benchmark's tolerances): aggregates, Galerkin matrices, colourings and
+ILU(0) factors bit-exact; FP64 residual histories within 1e-10 relative over
+the first 20 iterations; final solutions within 1e-8 relative.  Mixed
+precision runs must reach the FP64 true-residual tolerance; their distance
+to the FP64 oracle is reported.  Cases span several thread blocks and end in
+ragged tails (sizes not multiples of 32/128/256).
+"""
+import numpy as np
+import pytest
+
+from paper_1105_3468_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle as O
+    import paper_1105_3468_gb300 as amg
+    return amg, O, torch
+
+
+GRID_CASES = {
+    "c1-64": lambda: W.c1_block_2d_64(),
+    "rot2d-100": lambda: W.c2_rotating_2d_1024(n=100),
+    "aniso3d-13": lambda: W.c3_aniso_3d_128(n=13),
+}
+
+
+def _assemble(env, name):
+    amg, O, torch = env
+    p = GRID_CASES[name]()
+    A, b = amg.assemble_fv(p)
+    Ao, bo = O.fv_assemble(p)
+    return p, A, b, Ao, bo
+
+
+@pytest.mark.parametrize("name", sorted(GRID_CASES))
+def test_fv_assembly_bit_exact(env, name):
+    p, A, b, Ao, bo = _assemble(env, name)
+    assert np.array_equal(A.row_ptr.cpu().numpy(), Ao.row_ptr)
+    assert np.array_equal(A.col.cpu().numpy(), Ao.col)
+    assert np.array_equal(A.val.cpu().numpy(), Ao.val)
+    assert np.array_equal(b.cpu().numpy(), bo)
+
+
+def test_fv_grad_bit_exact(env):
+    amg, O, torch = env
+    p = W.c3_aniso_3d_128(n=9)
+    rng = np.random.default_rng(0)
+    lam, x = rng.standard_normal(p.n), rng.standard_normal(p.n)
+    ref = O.fv_grad_logk(p, lam, x)
+    d = lambda a: torch.as_tensor(a).cuda()
+    g = [torch.zeros(p.n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    amg.amg_fv_grad_logk(3, p.nx, p.ny, p.nz, d(p.kx), d(p.ky), d(p.kz), d(lam), d(x), *g)
+    torch.cuda.synchronize()
+    for a, r in zip(g, ref):
+        assert np.array_equal(a.cpu().numpy(), r)
+
+
+def test_spmv(env):
+    amg, O, torch = env
+    A = W.rgg_matrix(3001, 17, seed=3)
+    Ad = amg.CsrDevice.from_host(A)
+    x = np.random.default_rng(1).standard_normal(A.n)
+    y = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    amg.amg_spmv(Ad, torch.as_tensor(x).cuda(), y)
+    ref = O.spmv(A, x)
+    assert np.allclose(y.cpu().numpy(), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def _check_hierarchy(amg, O, h, H):
+    nlev = amg.amg_num_levels(h)
+    assert nlev == H.nlev
+    for l in range(nlev):
+        gi = amg.amg_get_level_info(h, l)
+        lo = H.levels[l]
+        assert gi["n"] == lo["n"] and gi["nnz"] == lo["nnz"] and bool(gi["dense"]) == lo["dense"]
+        rp, ci, v = amg.amg_get_matrix(h, l)
+        M = H.matrix(l)
+        assert np.array_equal(rp, M.row_ptr) and np.array_equal(ci, M.col)
+        assert np.array_equal(v, M.val), f"level {l} values differ"
+        if l + 1 < nlev:
+            assert np.array_equal(amg.amg_get_aggregates(h, l, 0), H.agg(l, 0)), f"level {l} aggregates"
+            assert np.array_equal(amg.amg_get_aggregates(h, l, 1), H.agg(l, 1))
+            assert np.array_equal(amg.amg_get_aggregates(h, l, 2), H.agg(l, 2))
+            rp1, ci1, v1 = amg.amg_get_pass_matrix(h, l, 1)
+            M1 = H.mid(l, 1)
+            assert np.array_equal(rp1, M1.row_ptr) and np.array_equal(ci1, M1.col) and np.array_equal(v1, M1.val)
+        if not lo["dense"]:
+            assert np.array_equal(amg.amg_get_colors(h, l), H.colors(l)), f"level {l} colours"
+            assert np.array_equal(amg.amg_get_ilu(h, l), H.lu(l)), f"level {l} ILU(0)"
+
+
+@pytest.mark.parametrize("name", sorted(GRID_CASES))
+def test_setup_bit_exact(env, name):
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, name)
+    h = amg.amg_setup(A)
+    H = O.Hierarchy(Ao)
+    _check_hierarchy(amg, O, h, H)
+
+
+def test_setup_bit_exact_rgg_and_first_fit(env):
+    amg, O, torch = env
+    A = W.rgg_matrix(4099, 11, seed=8)
+    h = amg.amg_setup(amg.CsrDevice.from_host(A), order_fine=amg.AMG_ORDER_COLOR,
+                      coloring=amg.AMG_COLOR_FIRST_FIT)
+    H = O.Hierarchy(A, order_fine=O.ORDER_COLOR, coloring=O.FIRST_FIT)
+    _check_hierarchy(amg, O, h, H)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name", sorted(GRID_CASES))
+def test_precond_apply(env, name):
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, name)
+    h = amg.amg_setup(A, build_adjoint=1)
+    H = O.Hierarchy(Ao)
+    z = np.random.default_rng(5).standard_normal(A.n)
+    zd = torch.as_tensor(z).cuda()
+    q = torch.zeros_like(zd)
+    amg.amg_precond_apply(h, zd, q)
+    assert _rel(q.cpu().numpy(), H.precond(z)) < 1e-11
+    amg.amg_precond_apply(h, zd, q, transpose=True)
+    assert _rel(q.cpu().numpy(), H.precond(z, transpose=True)) < 1e-11
+
+
+@pytest.mark.parametrize("name", sorted(GRID_CASES))
+def test_fgmres_fp64_history_and_solution(env, name):
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, name)
+    h = amg.amg_setup(A)
+    x = torch.zeros_like(b)
+    st = amg.amg_solve(h, b, x, 1e-8)
+    hist = amg.amg_get_history(h)
+    H = O.Hierarchy(Ao)
+    xo, info = H.fgmres(bo, tol=1e-8)
+    assert st.status == info.status == 0
+    assert st.iters == info.iters
+    k = min(21, len(hist))
+    rel = np.abs(hist[:k] - info.hist[:k]) / info.hist[:k]
+    assert rel.max() <= 1e-10, rel
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    assert st.rel_res_true <= 1e-8
+
+
+def test_adjoint_solution(env):
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, "rot2d-100")
+    h = amg.amg_setup(A, build_adjoint=1)
+    g = np.random.default_rng(2).standard_normal(A.n)
+    lam = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    st = amg.amg_adjoint(h, torch.as_tensor(g).cuda(), lam, 1e-10)
+    H = O.Hierarchy(Ao)
+    lo, info = H.fgmres(g, tol=1e-10, transpose=True)
+    assert st.status == 0 and info.status == 0
+    hist = amg.amg_get_history(h)
+    k = min(21, len(hist))
+    assert (np.abs(hist[:k] - info.hist[:k]) / info.hist[:k]).max() <= 1e-10
+    assert np.linalg.norm(lam.cpu().numpy() - lo) <= 1e-8 * np.linalg.norm(lo)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_precision_reaches_fp64_tolerance(env, prec):
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, "aniso3d-13")
+    vp = amg.AMG_FP32 if prec == "fp32" else amg.AMG_BF16
+    h64 = amg.amg_setup(A)
+    x64 = torch.zeros_like(b)
+    s64 = amg.amg_solve(h64, b, x64, 1e-8)
+    h = amg.amg_setup(A, vcycle_prec=vp)
+    x = torch.zeros_like(b)
+    st = amg.amg_solve(h, b, x, 1e-8)
+    assert st.status == 0 and st.rel_res_true <= 1e-8
+    # true residual recomputed independently of the library, in FP64 on the host
+    r = bo - O.spmv(Ao, x.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.0000001e-8 * np.linalg.norm(bo)
+    xo, _ = O.Hierarchy(Ao).fgmres(bo, tol=1e-8)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    print(f"{prec}: iters {st.iters} (fp64 {s64.iters}), |x - x_oracle|/|x_oracle| = {err:.2e}")
+    assert err < 1e-4
+    assert st.iters <= max(s64.iters + 3, int(1.5 * s64.iters))
+
+
+def test_edge_cases(env):
+    amg, O, torch = env
+    # diagonal matrix: no edges, coarsening stalls, last level solved exactly
+    n = 37
+    D = np.diag(np.arange(1, n + 1, dtype=float))
+    A = O.as_csr(D)
+    h = amg.amg_setup(amg.CsrDevice.from_host(A))
+    b = torch.arange(1, n + 1, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    st = amg.amg_solve(h, b, x, 1e-12)
+    assert st.status == 0 and np.allclose(x.cpu().numpy(), 1.0)
+    # 1 x 1
+    A1 = O.as_csr(np.array([[4.0]]))
+    h1 = amg.amg_setup(amg.CsrDevice.from_host(A1))
+    b1 = torch.tensor([2.0], dtype=torch.float64, device="cuda")
+    x1 = torch.zeros_like(b1)
+    assert amg.amg_solve(h1, b1, x1, 1e-12).status == 0 and abs(x1.item() - 0.5) < 1e-15
+    # zero right-hand side
+    p, A, b, Ao, bo = _assemble(env, "c1-64")
+    h = amg.amg_setup(A)
+    x = torch.ones_like(b)
+    st = amg.amg_solve(h, torch.zeros_like(b), x, 1e-8)
+    assert st.status == 0 and not x.any()
+    # maxit reached
+    h2 = amg.amg_setup(A, maxit=2)
+    x = torch.zeros_like(b)
+    st = amg.amg_solve(h2, b, x, 1e-8)
+    assert st.status == amg.AMG_ERR_NOT_CONVERGED and st.iters == 2
+    # NaN in b
+    bn = b.clone()
+    bn[7] = float("nan")
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_solve(h, bn, torch.zeros_like(b), 1e-8)
+    assert e.value.status == amg.AMG_ERR_NUMERIC
+
+
+def test_invalid_csr_rejected(env):
+    amg, O, torch = env
+    base = O.as_csr(np.array([[2.0, -1.0, 0.0], [-1.0, 2.0, -1.0], [0.0, -1.0, 2.0]]))
+    bad_cols = base._replace(col=base.col[[1, 0, 2, 3, 4, 5, 6]].copy())   # unsorted row 0
+    no_diag = O.as_csr(np.array([[0.0, 1.0], [1.0, 2.0]]))
+    out_of_range = base._replace(col=np.where(base.col == 2, 7, base.col).astype(np.int32))
+    for A in (bad_cols, no_diag, out_of_range):
+        with pytest.raises(amg.AmgError) as e:
+            amg.amg_setup(amg.CsrDevice.from_host(A))
+        assert e.value.status == amg.AMG_ERR_INVALID_ARG
+
+
+def test_host_buffers_e2e(env):
+    """The same call with host (numpy) buffers gives the same result."""
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, "c1-64")
+    h = amg.amg_setup(Ao)                      # host CSR
+    x = np.zeros(A.n)
+    st = amg.amg_solve(h, bo, x, 1e-8)
+    hd = amg.amg_setup(A)
+    xd = torch.zeros_like(b)
+    amg.amg_solve(hd, b, xd, 1e-8)
+    assert st.status == 0 and np.array_equal(x, xd.cpu().numpy())
