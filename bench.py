@@ -36,17 +36,20 @@ METRIC = "time-to-rel-residual 1e-8 (mixed vs FP64, same GPU); SpMV/cycle HBM GB
 
 
 def workload(name):
+    """(problem, tol, maxit, setup options, description)."""
     from paper_1105_3468_gb300 import workloads as W
     if name == "c3":
-        return (W.c3_aniso_3d_128(), 1e-8,
-                "fv3d-128^3-aniso-blockkappa (2,097,152 unknowns, 7-point upwind, 16^3 blocks "
-                "kappa_axis=10^U(-3,3), a=(1,1,1)), FP32 V-cycle in FP64 FGMRES(30), tol 1e-8")
+        return (W.c3_aniso_3d_128(), 1e-8, 3000, {},
+                "fv3d-128^3-aniso-blockkappa (2,097,152 unknowns, 14,581,760 nnz, 7-point upwind, 16^3 blocks "
+                "kappa_axis=10^U(-3,3), a=(1,1,1)); FGMRES(30) to true rel. residual 1e-8, maxit 3000; "
+                "natural-order ILU(0) on level 0, colour-major below")
     if name == "c2":
-        return (W.c2_rotating_2d_1024(), 1e-7,
+        return (W.c2_rotating_2d_1024(), 1e-7, 600, {"order_fine": 0},
                 "fv2d-1024^2-rotating (1,048,576 unknowns), FGMRES(30), tol 1e-7 "
-                "(1e-8 is below this matrix's FP64 attainable residual)")
+                "(1e-8 is below this matrix's FP64 attainable residual), colour-major ILU(0)")
     if name == "c1":
-        return W.c1_block_2d_64(), 1e-8, "fv2d-64^2-blockkappa (4096 unknowns), FGMRES(30), tol 1e-8"
+        return (W.c1_block_2d_64(), 1e-8, 600, {},
+                "fv2d-64^2-blockkappa (4096 unknowns), FGMRES(30), tol 1e-8")
     raise ValueError(name)
 
 
@@ -118,14 +121,14 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(prob, tol, iters_fp64, sample_iters=1):
+def cpu_baseline(prob, tol, iters_fp64, sopts, sample_iters=1):
     """Oracle (single-threaded C, as it stands) on a bounded sample: full-size
     setup plus `sample_iters` FGMRES iterations, scaled to the iteration count
     the method needs on this system."""
     import oracle as O
     A, b = O.fv_assemble(prob)
     t0 = time.perf_counter()
-    H = O.Hierarchy(A)
+    H = O.Hierarchy(A, **sopts)
     t1 = time.perf_counter()
     H.fgmres(b, tol=tol, maxit=sample_iters)
     t2 = time.perf_counter()
@@ -142,7 +145,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    prob, tol, desc = workload(args.workload)
+    prob, tol, maxit, sopts, desc = workload(args.workload)
     iters_path = os.path.join(ROOT, "oracle", "workload_iters.json")
     iters = json.load(open(iters_path)).get(args.workload) if os.path.exists(iters_path) else None
     if iters is None:
@@ -151,7 +154,7 @@ def run_reference(args):
     vals = []
     bl = None
     for k in range(args.warmup_ref + args.steps_ref):
-        bl = cpu_baseline(prob, tol, iters)
+        bl = cpu_baseline(prob, tol, iters, sopts)
         if k >= args.warmup_ref:
             vals.append(bl["value"])
     v = statistics.mean(vals)
@@ -168,13 +171,18 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--roofline-class", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--maxit", type=int, default=None, help="override the workload's iteration cap")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="one setup + solve of the workload (for ncu captures), no timing output")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--steps-ref", type=int, default=2)
     ap.add_argument("--warmup-ref", type=int, default=0)
     args = ap.parse_args()
@@ -198,13 +206,16 @@ def main():
         if world > 1:
             dist.barrier()
 
-    prob, tol, desc = workload(args.workload)
+    prob, tol, maxit, sopts, desc = workload(args.workload)
+    if args.maxit is not None:
+        maxit = args.maxit
     A, b = amg.assemble_fv(prob)
     torch.cuda.synchronize()
     vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
+    opts = dict(sopts, maxit=maxit)
 
     def step(prec, timing_class=0, acc=None):
-        h = amg.amg_setup(A, vcycle_prec=prec)
+        h = amg.amg_setup(A, vcycle_prec=prec, **opts)
         if timing_class:
             amg.amg_set_kernel_timing(h, timing_class)
         x = torch.zeros_like(b)
@@ -214,22 +225,29 @@ def main():
         h.close()
         return st
 
+    if args.profile_run:
+        st = step(vp)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": args.workload, "iters": st.iters, "status": st.status}))
+        return
+
     for _ in range(args.warmup):
         step(vp)
 
-    def timed(prec, timing_class=0):
+    def timed(prec, timing_class=0, steps=None):
+        steps = steps or args.steps
         stats, acc = [], []
         barrier()
         torch.cuda.synchronize()
         l0 = amg.amg_launch_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             stats.append(step(prec, timing_class, acc))
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         launches = amg.amg_launch_counter() - l0
         if world > 1:
             t = torch.tensor([ms], device="cuda")
@@ -240,16 +258,17 @@ def main():
     with ClockSampler(local) as clk:
         ms, stats, acc, launches = timed(vp, args.roofline_class)
     clocks = clk.summary()
-    ms64, stats64, _, _ = timed(amg.AMG_FP64) if vp != amg.AMG_FP64 else (ms, stats, None, None)
+    ms64, stats64, _, _ = (timed(amg.AMG_FP64, steps=args.fp64_steps) if vp != amg.AMG_FP64
+                           else (ms, stats, None, None))
 
     # end to end through the C ABI with host buffers (copies inside the region)
     Ah = amg.CsrDevice(A.n, A.row_ptr.cpu().numpy(), A.col.cpu().numpy(), A.val.cpu().numpy())
     bh = b.cpu().numpy()
     e2e = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, args.e2e_steps)):
         xh = np.zeros(A.n)
         t0 = time.perf_counter()
-        h = amg.amg_setup(Ah, vcycle_prec=vp)
+        h = amg.amg_setup(Ah, vcycle_prec=vp, **opts)
         amg.amg_solve(h, bh, xh, tol)
         h.close()
         e2e.append(1e3 * (time.perf_counter() - t0))
@@ -287,7 +306,7 @@ def main():
         "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(prob, tol, stats64[-1].iters)
+        out["cpu_baseline"] = cpu_baseline(prob, tol, stats64[-1].iters, sopts)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

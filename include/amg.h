@@ -8,11 +8,11 @@
  *   - problem: A x = b, A in R^{N x N} sparse, x, b in R^N (Section 1,
  *     eq. (1); Algorithm 1, its title);
  *   - setup: aggregates from graph matching (Section 2), prolongation P with
- *     P_ij = 1 iff i in G_j (Section 2, definition of P and eq. (3)),
- *     Galerkin coarse matrix A_c = P^T A P (eq. (1) of Section 2 and its
+ *     P_ij = 1 iff i in G_j (Section 2, definition of P and eq. (4)),
+ *     Galerkin coarse matrix A_c = P^T A P (eq. (3) of Section 2 and its
  *     entrywise form), ILU(0) smoother S = L0 U0 (Algorithm 1, setup);
  *   - preconditioner B~ = (S^{-1} + M~^{-1} - M~^{-1} A S^{-1})^{-1} without
- *     post-smoothing, M~ = P A~_c P^T (eq. (4), Algorithm 1 "SOLVE B~q=z"
+ *     post-smoothing, M~ = P A~_c P^T (eq. (5), Algorithm 1 "SOLVE B~q=z"
  *     and "SOLVE M~g=h");
  *   - Krylov accelerator: GMRES with Givens rotations (Algorithm 1), here
  *     the flexible right-preconditioned variant FGMRES(m).
@@ -105,8 +105,12 @@ typedef struct {
     int32_t maxit;            /* total inner iterations cap: 600           */
     int32_t vcycle_prec;      /* AMG_FP64 / AMG_FP32 / AMG_BF16: AMG_FP64  */
     int32_t build_adjoint;    /* nonzero: also build transposed structures */
-    int32_t use_graphs;       /* nonzero: replay the inner iteration as a CUDA graph */
-    int32_t reserved0;
+    int32_t use_graphs;       /* nonzero: replay the inner iteration as a CUDA
+                                 graph captured once per handle: 1          */
+    int32_t persistent;       /* nonzero: each ILU(0) smoother application
+                                 is one cooperative kernel with a bounded
+                                 grid barrier between schedule levels; a
+                                 wait that gives up returns AMG_ERR_LIMIT: 1 */
     uint64_t seed;            /* tie-break seed, default 0                 */
 } amg_options_t;
 
@@ -210,8 +214,8 @@ int amg_get_ilu(amg_handle_t *h, int32_t level, double *out);
 /* ------------------------------------------------------------ profiling */
 /* Times one kernel class with CUDA events on the handle's stream (for a
  * roofline figure measured while solving): 0 off, 1 the outer FP64 SpMV
- * w = A z_j, 2 the level-0 ILU(0) forward+backward sweeps of one
- * preconditioner application, 3 one CGS2 orthogonalisation pass.  Setting
+ * w = A z_j, 2 every ILU(0) smoother application (forward + backward
+ * solve) on every level, 3 one CGS2 orthogonalisation pass.  Setting
  * a class clears the totals.  No effect on results.  Errors:
  * AMG_ERR_INVALID_ARG. */
 int amg_set_kernel_timing(amg_handle_t *h, int32_t kclass);

@@ -213,7 +213,7 @@ def match(A, seed: int = 0):
 
 
 def aggregate(mate):
-    """Aggregates from a matching, numbered by smallest member (eq. (3))."""
+    """Aggregates from a matching, numbered by smallest member (eq. (4))."""
     mate = np.ascontiguousarray(mate, dtype=np.int32)
     agg = np.zeros(mate.size, np.int32)
     nc = lib().or_aggregate(mate.size, mate, agg)

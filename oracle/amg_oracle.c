@@ -350,7 +350,7 @@ int64_t or_match(int n, const int64_t *rp, const int32_t *ci, const double *v,
 }
 
 /* ------------------------------------------------------------------ */
-/* O3. Aggregates from a matching (eq. (3) partition; the "part" map of */
+/* O3. Aggregates from a matching (eq. (4) partition; the "part" map of */
 /* Section 2): each pair or singleton is one aggregate, numbered in     */
 /* ascending order of its smallest member.  Returns N_c.                */
 /* ------------------------------------------------------------------ */
@@ -365,7 +365,7 @@ int or_aggregate(int n, const int32_t *mate, int32_t *agg)
 }
 
 /* ------------------------------------------------------------------ */
-/* O4. Galerkin coarse matrix A_c = P^T A P (eq. (1)) in its entrywise  */
+/* O4. Galerkin coarse matrix A_c = P^T A P (eq. (3)) in its entrywise  */
 /* form (A_c)_IJ = sum_{k in G_I} sum_{l in G_J} a_kl (Section 2).       */
 /* Entries of A in row-major, ascending-column order are stably sorted   */
 /* by (agg[k], agg[l]); equal keys are summed sequentially in that       */
@@ -868,7 +868,7 @@ void or_hier_lu(const or_hier_t *H, int l, double *out)
 /* O6. Preconditioner.  Algorithm 1 (SOLVE B~q = z) computes            */
 /*   S t = z; M~ f = z; M~ q' = A t; q = t + f - q'                      */
 /* with M~^{-1} = P A~_c^{-1} P^T linear, so q = t + M~^{-1}(z - A t):   */
-/* one coarse solve of the restricted residual (eq. (4), inexact M~).    */
+/* one coarse solve of the restricted residual (eq. (5), inexact M~).    */
 /* At level l:                                                           */
 /*   t = S_l^{-1} z        ILU(0) forward/backward sweep                 */
 /*   r = z - A_l t                                                       */

@@ -37,10 +37,10 @@ class AmgOptions(C.Structure):
                 ("dense_max", C.c_int32), ("max_levels", C.c_int32), ("order_fine", C.c_int32),
                 ("order_coarse", C.c_int32), ("coloring", C.c_int32), ("restart", C.c_int32),
                 ("maxit", C.c_int32), ("vcycle_prec", C.c_int32), ("build_adjoint", C.c_int32),
-                ("use_graphs", C.c_int32), ("reserved0", C.c_int32), ("seed", C.c_uint64)]
+                ("use_graphs", C.c_int32), ("persistent", C.c_int32), ("seed", C.c_uint64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved0"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class AmgStats(C.Structure):

@@ -54,14 +54,22 @@ struct Level {
 
 struct amg_handle {
     amg_options_t opt;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;        // internal non-blocking stream (all library work)
+    cudaStream_t ustream = nullptr;       // the caller's stream given to amg_setup
+    cudaEvent_t entry_ev = nullptr;
     std::vector<std::unique_ptr<amg::Level>> lev;
     int n = 0;
     // FGMRES storage
-    amg::DBuf<double> V, Zd, w, r, xb, bb, hist, partials;
-    amg::DBuf<float> Zf, zin32;
+    amg::DBuf<double> V, Zd, w, r, xb, bb, hist, partials, zin64, zout64;
+    amg::DBuf<float> Zf, zin32, zout32;
+    int *hflags = nullptr;                // pinned: stop flag, status
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // inner iteration (solve, adjoint)
+    size_t gpairs[2] = {0, 0};            // timing event pairs recorded by each graph
+    int64_t gnodes[2] = {0, 0};           // kernels in each graph
+    double gbytes[2] = {0.0, 0.0};        // timed-class bytes of one replay
     amg::DBuf<amg::FgState> st;
-    amg::DBuf<unsigned int> ticket;
+    amg::DBuf<unsigned int> ticket, bar;   // reduction ticket; grid-barrier words
+    amg::DBuf<int> err;                      // set when a device wait gives up
     amg::FgState *hst = nullptr;          // pinned host mirror
     std::vector<double> last_hist;
     double setup_ms = 0.0;
@@ -84,6 +92,13 @@ static bool is_device_ptr(const void *p) {
     cudaError_t e = cudaPointerGetAttributes(&a, p);
     if (e != cudaSuccess) { cudaGetLastError(); return false; }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Orders the handle's internal stream after the work already queued on the
+// caller's stream (inputs may still be in flight there).
+static void enter(amg_handle *h) {
+    CU(cudaEventRecord(h->entry_ev, h->ustream));
+    CU(cudaStreamWaitEvent(h->stream, h->entry_ev, 0));
 }
 
 template <typename T>
@@ -324,14 +339,19 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
     }
     const size_t n = h->n, m = o.restart;
     h->V.alloc((m + 1) * n);
-    if (o.vcycle_prec == AMG_FP64) h->Zd.alloc(m * n);
-    else { h->Zf.alloc(m * n); h->zin32.alloc(n); }
+    if (o.vcycle_prec == AMG_FP64) { h->Zd.alloc(m * n); h->zin64.alloc(n); h->zout64.alloc(n); }
+    else { h->Zf.alloc(m * n); h->zin32.alloc(n); h->zout32.alloc(n); }
+    CU(cudaMallocHost(&h->hflags, 2 * sizeof(int)));
     h->w.alloc(n); h->r.alloc(n); h->xb.alloc(n); h->bb.alloc(n);
     h->hist.alloc((size_t)o.maxit + 2);
     h->partials.alloc((size_t)reduce_grid() * KMAX1);
     h->st.alloc(1);
     h->ticket.alloc(1);
     CU(cudaMemsetAsync(h->ticket.get(), 0, sizeof(unsigned int), s));
+    h->bar.alloc(2);
+    CU(cudaMemsetAsync(h->bar.get(), 0, 2 * sizeof(unsigned int), s));
+    h->err.alloc(1);
+    CU(cudaMemsetAsync(h->err.get(), 0, sizeof(int), s));
     CU(cudaMallocHost(&h->hst, sizeof(FgState)));
     CU(cudaStreamSynchronize(s));
 }
@@ -345,23 +365,33 @@ static void tmark_begin(amg_handle *h, int kclass) {
         CU(cudaEventCreate(&b));
         h->tev.emplace_back(a, b);
     }
-    CU(cudaEventRecord(h->tev[h->tused].first, h->stream));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(h->stream, &cs));
+    // inside a capture the record must become a node of the graph
+    CU(cudaEventRecordWithFlags(h->tev[h->tused].first, h->stream,
+                                cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0));
 }
 static void tmark_end(amg_handle *h, int kclass, double bytes) {
     if (h->tclass != kclass) return;
-    CU(cudaEventRecord(h->tev[h->tused].second, h->stream));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(h->stream, &cs));
+    CU(cudaEventRecordWithFlags(h->tev[h->tused].second, h->stream,
+                                cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0));
     ++h->tused;
     h->t_bytes += bytes;
     h->t_bytes_per_launch = bytes;
 }
 // after a synchronisation: fold the recorded pairs into the totals
-static void tcollect(amg_handle *h) {
-    for (size_t i = 0; i < h->tused; ++i) {
+static void tcollect(amg_handle *h, size_t count) {
+    for (size_t i = 0; i < count; ++i) {
         float ms = 0.f;
         CU(cudaEventElapsedTime(&ms, h->tev[i].first, h->tev[i].second));
         h->t_ms += ms;
         ++h->t_launches;
     }
+}
+static void tcollect(amg_handle *h) {
+    tcollect(h, h->tused);
     h->tused = 0;
 }
 
@@ -383,6 +413,26 @@ struct VCycle {
     SweepView<T, V> view(Sweep &S);
 
     int nlev() const { return (int)h->lev.size(); }
+
+    // t = S^{-1} in (transpose: S^{-T} in); y is scratch for the first solve
+    void smooth(Level &Lv, const T *in, T *y, T *t, bool transpose) {
+        Sweep &F = transpose ? Lv.fwdT : Lv.fwd;
+        Sweep &B = transpose ? Lv.bwdT : Lv.bwd;
+        const int fd = transpose ? 1 : 0, bd = transpose ? 0 : 1;
+        // algorithmic bytes: factor values + columns + schedule rows/pointers,
+        // the diagonal, in read once, y written and read, out written
+        const double n = Lv.A.n;
+        const double bytes = (sizeof(V) + 4.0) * (double)(F.v64.n + B.v64.n) + 12.0 * 2.0 * n +
+                             sizeof(T) * (1.0 + (B.d64.n || F.d64.n ? 1.0 : 0.0) + 3.0) * n;
+        tmark_begin(h, 2);
+        if (h->opt.persistent) {
+            sweep_pair_coop<T, V>(view(F), fd, view(B), bd, in, y, t, h->bar.get(), h->err.get(), s);
+        } else {
+            sweep<T, V>(view(F), in, y, fd, s);
+            sweep<T, V>(view(B), y, t, bd, s);
+        }
+        tmark_end(h, 2, bytes);
+    }
     bool has_child(int l) { return l + 1 < nlev() && L(l).n_next > 0; }
 
     // q (mode 0: =, mode 1: +=) B_l^{-1} z
@@ -390,15 +440,7 @@ struct VCycle {
         Level &Lv = L(l);
         const int n = Lv.A.n;
         T *y = ws(Lv.wy), *t = ws(Lv.wt), *r = ws(Lv.wr);
-        if (l == 0) tmark_begin(h, 2);
-        sweep<T, V>(view(Lv.fwd), z, y, 0, s);
-        sweep<T, V>(view(Lv.bwd), y, t, 1, s);
-        if (l == 0) {
-            // factors (values + columns + row pointers + diagonal), z, y, t
-            const double vb = sizeof(V) + 4.0;
-            tmark_end(h, 2, vb * (double)(Lv.fwd.v64.n + Lv.bwd.v64.n) + 8.0 * (2.0 * n + 2.0) +
-                                sizeof(T) * (double)n * 5.0);
-        }
+        smooth(Lv, z, y, t, false);
         level_residual<T, V>(mats(l, false), t, z, r, s);
         Level &C = L(l + 1);
         T *hc = ws(C.wh), *gc = ws(C.wg);
@@ -423,8 +465,7 @@ struct VCycle {
                 precond(l, in, g, it == 0 ? 0 : 1);
             } else {
                 T *y = ws(Lv.wy), *t = ws(Lv.wt);
-                sweep<T, V>(view(Lv.fwd), in, y, 0, s);
-                sweep<T, V>(view(Lv.bwd), y, t, 1, s);
+                smooth(Lv, in, y, t, false);
                 vec_acc<T>(Lv.A.n, t, g, it == 0 ? 0 : 1, s);
             }
         }
@@ -441,8 +482,7 @@ struct VCycle {
         level_solveT(l + 1, hc, gc);
         prolong<T, T>(n, Lv.agg.get(), nullptr, gc, f, 2, s);
         level_residual<T, V>(mats(l, true), f, z, r, s);
-        sweep<T, V>(view(Lv.fwdT), r, y, 1, s);
-        sweep<T, V>(view(Lv.bwdT), y, t, 0, s);
+        smooth(Lv, r, y, t, true);
         // q (mode)= f + t
         prolong<T, T>(n, nullptr, f, t, q, mode == 0 ? 3 : 4, s);
     }
@@ -462,8 +502,7 @@ struct VCycle {
                 precondT(l, in, g, it == 0 ? 0 : 1);
             } else {
                 T *y = ws(Lv.wy), *t = ws(Lv.wt);
-                sweep<T, V>(view(Lv.fwdT), in, y, 1, s);
-                sweep<T, V>(view(Lv.bwdT), y, t, 0, s);
+                smooth(Lv, in, y, t, true);
                 vec_acc<T>(Lv.A.n, t, g, it == 0 ? 0 : 1, s);
             }
         }
@@ -476,59 +515,111 @@ template <> const __nv_bfloat16 *VCycle<float, __nv_bfloat16>::vals(Level &Lv, b
     return tr ? Lv.vt16.get() : Lv.v16.get();
 }
 template <> SweepView<double, double> VCycle<double, double>::view(Sweep &S) {
-    return SweepView<double, double>{S.nlev, S.lev_ptr.data(), S.rows.get(), S.rp.get(), S.ci.get(), S.v64.get(),
-                                     S.d64.n ? S.d64.get() : nullptr};
+    return SweepView<double, double>{S.nlev, S.lev_ptr.data(), S.dlev.get(), S.rows.get(), S.rp.get(), S.ci.get(),
+                                     S.v64.get(), S.d64.n ? S.d64.get() : nullptr};
 }
 template <> SweepView<float, float> VCycle<float, float>::view(Sweep &S) {
-    return SweepView<float, float>{S.nlev, S.lev_ptr.data(), S.rows.get(), S.rp.get(), S.ci.get(), S.v32.get(),
-                                   S.d32.n ? S.d32.get() : nullptr};
+    return SweepView<float, float>{S.nlev, S.lev_ptr.data(), S.dlev.get(), S.rows.get(), S.rp.get(), S.ci.get(),
+                                   S.v32.get(), S.d32.n ? S.d32.get() : nullptr};
 }
 template <> SweepView<float, __nv_bfloat16> VCycle<float, __nv_bfloat16>::view(Sweep &S) {
-    return SweepView<float, __nv_bfloat16>{S.nlev, S.lev_ptr.data(), S.rows.get(), S.rp.get(), S.ci.get(),
-                                           S.v16.get(), S.d32.n ? S.d32.get() : nullptr};
+    return SweepView<float, __nv_bfloat16>{S.nlev, S.lev_ptr.data(), S.dlev.get(), S.rows.get(), S.rp.get(),
+                                           S.ci.get(), S.v16.get(), S.d32.n ? S.d32.get() : nullptr};
 }
 
-// Preconditioner application at level 0 with FP64 input; output z in the
-// V-cycle type (zout) or FP64 (zout64).
+// q = B~^{-1} zin (or B~^{-T} zin) at level 0 in the V-cycle type.
 template <typename T, typename V>
-static void apply_level0(amg_handle *h, const double *vin, T *zout, bool transpose) {
-    VCycle<T, V> vc{h, h->stream};
-    const T *zin;
-    if constexpr (sizeof(T) == sizeof(double)) {
-        zin = reinterpret_cast<const T *>(vin);
-    } else {
-        convert_f64_f32(h->n, vin, h->zin32.get(), h->stream);
-        zin = reinterpret_cast<const T *>(h->zin32.get());
-    }
+static void precond0(amg_handle *h, const T *zin, T *zout, bool transpose) {
     if (h->lev.size() < 2) fail(AMG_ERR_NOT_SUPPORTED, "hierarchy has a single level");
+    VCycle<T, V> vc{h, h->stream};
     if (transpose) vc.precondT(0, zin, zout, 0);
     else vc.precond(0, zin, zout, 0);
 }
 
-static void apply_precond(amg_handle *h, const double *vin, int j, bool transpose) {
-    const size_t n = h->n;
+static void apply_precond_vtype(amg_handle *h, bool transpose) {
     switch (h->opt.vcycle_prec) {
-    case AMG_FP64: apply_level0<double, double>(h, vin, h->Zd.get() + (size_t)j * n, transpose); break;
-    case AMG_FP32: apply_level0<float, float>(h, vin, h->Zf.get() + (size_t)j * n, transpose); break;
-    default: apply_level0<float, __nv_bfloat16>(h, vin, h->Zf.get() + (size_t)j * n, transpose); break;
+    case AMG_FP64: precond0<double, double>(h, h->zin64.get(), h->zout64.get(), transpose); break;
+    case AMG_FP32: precond0<float, float>(h, h->zin32.get(), h->zout32.get(), transpose); break;
+    default: precond0<float, __nv_bfloat16>(h, h->zin32.get(), h->zout32.get(), transpose); break;
     }
 }
 
 // ------------------------------------------------------------------ FGMRES
-static void outer_spmv_z(amg_handle *h, int j, double *y, bool transpose) {
+// One inner FGMRES iteration (column j = st->j, read on the device):
+// z_j = B~^{-1} v_j, w = A z_j, CGS2 against v_0..v_j, ||w||, Givens,
+// v_{j+1} = w / ||w||, and the stop flag copied to pinned host memory.
+static void enqueue_iteration(amg_handle *h, bool transpose) {
+    cudaStream_t s = h->stream;
+    const size_t n = h->n;
+    FgState *dst = h->st.get();
     Level &L0 = *h->lev[0];
     const DCsr &M = transpose ? L0.AT : L0.A;
-    const size_t n = h->n;
-    const double xs = h->opt.vcycle_prec == AMG_FP64 ? 8.0 : 4.0;
-    // algorithmic bytes: values + columns, row pointers, x read once, y written once
-    const double bytes = 12.0 * M.nnz + 4.0 * (M.n + 1) + xs * M.n + 8.0 * M.n;
+    const bool f64 = h->opt.vcycle_prec == AMG_FP64;
+    if (f64) load_vj<double>(n, dst, h->V.get(), h->zin64.get(), s);
+    else load_vj<float>(n, dst, h->V.get(), h->zin32.get(), s);
+    apply_precond_vtype(h, transpose);
+    // algorithmic bytes of w = A z: values + columns, row pointers, z once, w once
+    const double bytes = 12.0 * M.nnz + 4.0 * (M.n + 1) + (f64 ? 8.0 : 4.0) * M.n + 8.0 * M.n;
     tmark_begin(h, 1);
-    if (h->opt.vcycle_prec == AMG_FP64)
-        spmv_f64(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), h->Zd.get() + j * n, y, h->stream);
-    else
-        spmv_f64_xf32(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), h->Zf.get() + j * n, y, h->stream);
+    if (f64) spmv_f64(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), h->zout64.get(), h->w.get(), s);
+    else spmv_f64_xf32(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), h->zout32.get(), h->w.get(), s);
     tmark_end(h, 1, bytes);
+    if (f64) store_zj<double>(n, dst, h->zout64.get(), h->Zd.get(), s);
+    else store_zj<float>(n, dst, h->zout32.get(), h->Zf.get(), s);
+    mdot(n, dst, h->w.get(), h->V.get(), n, h->partials.get(), h->ticket.get(), dst->h1, s);
+    // a CGS2 pass reads the K = j+1 basis vectors and w and writes w; K is
+    // known only on the device, so the bytes use the cycle's mean K = (m+1)/2
+    tmark_begin(h, 3);
+    cgs_update(n, dst, dst->h1, h->w.get(), h->V.get(), n, 1, h->partials.get(), h->ticket.get(), dst->h2, s);
+    tmark_end(h, 3, 8.0 * (double)n * (0.5 * (h->opt.restart + 1) + 2.0));
+    cgs_update(n, dst, dst->h2, h->w.get(), h->V.get(), n, 0, h->partials.get(), h->ticket.get(), dst->nrm2, s);
+    givens(dst, s);
+    scale_next(n, h->w.get(), h->V.get(), dst, s);
+    CU(cudaMemcpyAsync(h->hflags, &dst->stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
 }
+
+// Runs one inner iteration, replaying a captured CUDA graph when enabled.
+static void run_iteration(amg_handle *h, bool transpose) {
+    const int d = transpose ? 1 : 0;
+    if (!h->opt.use_graphs) {
+        enqueue_iteration(h, transpose);
+        CU(cudaStreamSynchronize(h->stream));
+        tcollect(h);
+        return;
+    }
+    if (!h->gexec[d]) {
+        const size_t before = h->tused;
+        const int64_t l0 = launch_count();
+        const double b0 = h->t_bytes;
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue_iteration(h, transpose);
+        } catch (...) {
+            cudaStreamEndCapture(h->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            h->tused = before;
+            throw;
+        }
+        CU(cudaStreamEndCapture(h->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&h->gexec[d], g, 0);
+        cudaGraphDestroy(g);
+        CU(e);
+        h->gpairs[d] = h->tused - before;
+        h->tused = before;
+        h->gnodes[d] = launch_count() - l0;
+        count_launch(-h->gnodes[d]);          // counted again at each replay
+        h->gbytes[d] = h->t_bytes - b0;
+        h->t_bytes = b0;                      // added again at each replay
+    }
+    CU(cudaGraphLaunch(h->gexec[d], h->stream));
+    count_launch(h->gnodes[d]);
+    h->t_bytes += h->gbytes[d];
+    CU(cudaStreamSynchronize(h->stream));
+    tcollect(h, h->gpairs[d]);
+}
+
 static void outer_residual(amg_handle *h, const double *b, const double *x, double *r, bool transpose) {
     Level &L0 = *h->lev[0];
     const DCsr &M = transpose ? L0.AT : L0.A;
@@ -546,6 +637,7 @@ static double read_norm(amg_handle *h, const double *v) {
 
 static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, amg_stats_t *stats, bool transpose) {
     const auto t0 = std::chrono::steady_clock::now();
+    enter(h);
     const int64_t launches0 = launch_count();
     cudaStream_t s = h->stream;
     const size_t n = h->n;
@@ -587,27 +679,9 @@ static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, a
             if (total >= h->opt.maxit) { status = AMG_ERR_NOT_CONVERGED; break; }
             // the state's nrm2 holds ||r||^2 from read_norm
             restart_scale(n, h->r.get(), h->V.get(), dst, s);
-            int j = 0;
-            for (; j < m; ++j) {
-                double *vj = h->V.get() + (size_t)j * n;
-                apply_precond(h, vj, j, transpose);
-                outer_spmv_z(h, j, h->w.get(), transpose);
-                mdot(n, j + 1, h->w.get(), h->V.get(), n, h->partials.get(), h->ticket.get(), dst->h1, s);
-                // CGS2: reads K basis vectors and w, writes w
-                const double cbytes = 8.0 * (double)n * (j + 1) + 16.0 * (double)n;
-                tmark_begin(h, 3);
-                cgs_update(n, j + 1, dst->h1, h->w.get(), h->V.get(), n, 1, h->partials.get(), h->ticket.get(), dst->h2, s);
-                tmark_end(h, 3, cbytes);
-                tmark_begin(h, 3);
-                cgs_update(n, j + 1, dst->h2, h->w.get(), h->V.get(), n, 0, h->partials.get(), h->ticket.get(), dst->nrm2, s);
-                tmark_end(h, 3, cbytes);
-                givens(dst, j, s);
-                scale_next(n, h->w.get(), h->V.get() + (size_t)(j + 1) * n, dst, s);
-                int flags[2];
-                CU(cudaMemcpyAsync(flags, &dst->stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-                CU(cudaStreamSynchronize(s));
-                tcollect(h);
-                if (flags[0]) { ++j; break; }
+            for (int j = 0; j < m; ++j) {
+                run_iteration(h, transpose);
+                if (h->hflags[0]) break;
             }
             CU(cudaMemcpyAsync(&hs, dst, sizeof(FgState), cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
@@ -632,7 +706,16 @@ static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, a
     }
     if (x_dev) CU(cudaMemcpyAsync(x_io, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     else CU(cudaMemcpyAsync(x_io, x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    int derr = 0;
+    CU(cudaMemcpyAsync(&derr, h->err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (derr) {
+        CU(cudaMemsetAsync(h->err.get(), 0, sizeof(int), s));
+        CU(cudaMemsetAsync(h->bar.get(), 0, 2 * sizeof(unsigned int), s));
+        CU(cudaStreamSynchronize(s));
+        t_last_error = "a grid-barrier wait gave up (results invalid)";
+        status = AMG_ERR_LIMIT;
+    }
     const auto t1 = std::chrono::steady_clock::now();
     if (stats) {
         stats->status = status;
@@ -707,7 +790,8 @@ int amg_default_options(amg_options_t *o) {
     o->maxit = 600;
     o->vcycle_prec = AMG_FP64;
     o->build_adjoint = 0;
-    o->use_graphs = 0;
+    o->use_graphs = 1;
+    o->persistent = 1;
     o->seed = 0;
     return AMG_OK;
 }
@@ -729,7 +813,10 @@ int amg_setup(const amg_csr_t *A, const amg_options_t *opt, void *stream, amg_ha
     if (opt) h->opt = *opt;
     else amg_default_options(&h->opt);
     check_options(h->opt);
-    h->stream = (cudaStream_t)stream;
+    h->ustream = (cudaStream_t)stream;
+    CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&h->entry_ev, cudaEventDisableTiming));
+    enter(h.get());
     setup_impl(h.get(), A);
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h.release();
@@ -742,6 +829,12 @@ void amg_destroy(amg_handle_t *h) {
     try {
         cudaStreamSynchronize(h->stream);
         if (h->hst) cudaFreeHost(h->hst);
+        if (h->hflags) cudaFreeHost(h->hflags);
+        for (auto &g : h->gexec) if (g) cudaGraphExecDestroy(g);
+        h->lev.clear();
+        h->V.release(); h->Zd.release(); h->Zf.release();
+        if (h->entry_ev) cudaEventDestroy(h->entry_ev);
+        if (h->stream) cudaStreamDestroy(h->stream);
         for (auto &e : h->tev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
         delete h;
     } catch (...) {
@@ -779,12 +872,17 @@ int amg_precond_apply(amg_handle_t *h, const double *z, double *q, int32_t trans
     if (!h || !z || !q) fail(AMG_ERR_INVALID_ARG, "amg_precond_apply: null argument");
     if (transpose && !h->adjoint_ready) fail(AMG_ERR_INVALID_ARG, "amg_precond_apply: no adjoint structures");
     if (!is_device_ptr(z) || !is_device_ptr(q)) fail(AMG_ERR_INVALID_ARG, "amg_precond_apply: device pointers required");
-    apply_precond(h, z, 0, transpose != 0);
+    enter(h);
     const size_t n = h->n;
-    if (h->opt.vcycle_prec == AMG_FP64)
-        CU(cudaMemcpyAsync(q, h->Zd.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    else
-        convert_f32_f64(n, h->Zf.get(), q, h->stream);
+    if (h->opt.vcycle_prec == AMG_FP64) {
+        CU(cudaMemcpyAsync(h->zin64.get(), z, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        apply_precond_vtype(h, transpose != 0);
+        CU(cudaMemcpyAsync(q, h->zout64.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        convert_f64_f32(n, z, h->zin32.get(), h->stream);
+        apply_precond_vtype(h, transpose != 0);
+        convert_f32_f64(n, h->zout32.get(), q, h->stream);
+    }
     CU(cudaStreamSynchronize(h->stream));
     return AMG_OK;
     ABI_CATCH

@@ -78,6 +78,7 @@ struct DCsr {
 struct Sweep {
     int nlev = 0;                   // schedule levels
     std::vector<int> lev_ptr;       // host copy [nlev+1] into rows
+    DBuf<int> dlev;                 // device copy of lev_ptr
     DBuf<int> rows;                 // [n] row ids in schedule order
     DBuf<int> rp;                   // [n+1] entries of rows[k] at rp[k]..rp[k+1]
     DBuf<int> ci;                   // [nnzf] column ids

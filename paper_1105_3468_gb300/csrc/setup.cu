@@ -599,11 +599,10 @@ static void build_sweep(const DCsr &A, const int *pos, const double *lu, int fwd
     CU_LAUNCH("k_int_to_key"); count_launch();
     iota_int(S.rows.get(), n, s);
     if (nlev > 1) radix_sort_pairs(keys.get(), S.rows.get(), n, bits_for((uint32_t)nlev), s);
-    DBuf<int> lp;
-    segment_ptr(keys.get(), n, nlev, lp, s);
+    segment_ptr(keys.get(), n, nlev, S.dlev, s);
     S.nlev = nlev;
     S.lev_ptr.resize(nlev + 1);
-    CU(cudaMemcpyAsync(S.lev_ptr.data(), lp.get(), sizeof(int) * (nlev + 1), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(S.lev_ptr.data(), S.dlev.get(), sizeof(int) * (nlev + 1), cudaMemcpyDeviceToHost, s));
     DBuf<int> cnt(n + 1);
     fill_int(cnt.get(), 0, n + 1, s);
     k_sweep_count<<<grid_for(n, 256), 256, 0, s>>>(n, S.rows.get(), A.rp.get(), A.ci.get(), pos, fwd, cnt.get());

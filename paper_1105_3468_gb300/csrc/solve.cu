@@ -110,6 +110,149 @@ void sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag, cudaStr
     CU_LAUNCH("k_sweep"); count_launch(S.nlev);
 }
 template void sweep<double, double>(const SweepView<double, double> &, const double *, double *, int, cudaStream_t);
+
+// ------------------------------------------------------------------ persistent sweeps
+// Grid barrier for a cooperative launch (all blocks resident).  bar[0]
+// counts arrivals, bar[1] is the generation.  A wait gives up after
+// SPIN_LIMIT polls and sets *err; once *err is set every later barrier
+// returns at once, so the kernel always terminates.
+constexpr unsigned int SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int gen, arrived;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
+        // arrival releases this block's writes (ordered before by bar.sync) and
+        // acquires those of the blocks that arrived earlier
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+        if (arrived + 1u == gridDim.x) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(bar), "r"(0u) : "memory");
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(gen + 1u) : "memory");
+        } else {
+            unsigned int spins = 0;
+            while (ld_acquire_gpu(bar + 1) == gen) {
+                if (*(volatile int *)err) break;
+                if (++spins > SPIN_LIMIT) { atomicExch(err, 1); break; }
+                if (spins > 64) __nanosleep(20);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T> __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
+
+// Rows of one schedule level; out values written by earlier levels of this
+// launch are read past L1 (__ldcg), since L1 is not coherent across SMs.
+template <typename T, typename V>
+__device__ __forceinline__ void sweep_level_rows(int b, int e, const int *__restrict__ rows, const int *__restrict__ rp,
+                                                 const int *__restrict__ ci, const V *__restrict__ v,
+                                                 const T *__restrict__ dg, const T *in, bool in_coherent, T *out,
+                                                 int with_diag, int tid, int nthr) {
+    for (int t = b + tid; t < e; t += nthr) {
+        const int i = rows[t];
+        T acc = in_coherent ? ld_cg(in + i) : in[i];
+        const int e1 = rp[t + 1];
+        for (int k = rp[t]; k < e1; ++k) acc -= val_as<T, V>(v[k]) * ld_cg(out + ci[k]);
+        out[i] = with_diag ? acc / dg[t] : acc;
+    }
+}
+
+// One triangular solve over all schedule levels of S.  The first row a
+// thread owns in the next level is prefetched (row id, extent, up to PF
+// columns and values, diagonal, and the input when it is not produced by this
+// launch) before the barrier, so that after the barrier only the values of
+// earlier rows remain to be loaded.
+constexpr int SWEEP_PF = 4;
+
+template <typename T, typename V>
+__device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, int with_diag, const T *in, bool in_coherent,
+                                            T *out, unsigned int *bar, int *err, int tid, int nthr, bool last_barrier) {
+    int pt = -1, pi = 0, pk0 = 0, pk1 = 0, pc[SWEEP_PF];
+    V pv[SWEEP_PF];
+    T pd = T(1), pin = T(0);
+    auto prefetch = [&](int l) {
+        pt = -1;
+        if (l >= S.nlev) return;
+        const int t = S.dlev[l] + tid;
+        if (t >= S.dlev[l + 1]) return;
+        pt = t;
+        pi = S.rows[t];
+        pk0 = S.rp[t];
+        pk1 = S.rp[t + 1];
+#pragma unroll
+        for (int q = 0; q < SWEEP_PF; ++q)
+            if (pk0 + q < pk1) { pc[q] = S.ci[pk0 + q]; pv[q] = S.v[pk0 + q]; }
+        if (with_diag) pd = S.d[t];
+        if (!in_coherent) pin = in[pi];
+    };
+    prefetch(0);
+    for (int l = 0; l < S.nlev; ++l) {
+        if (pt >= 0) {
+            T acc = in_coherent ? ld_cg(in + pi) : pin;
+#pragma unroll
+            for (int q = 0; q < SWEEP_PF; ++q)
+                if (pk0 + q < pk1) acc -= val_as<T, V>(pv[q]) * ld_cg(out + pc[q]);
+            for (int k = pk0 + SWEEP_PF; k < pk1; ++k) acc -= val_as<T, V>(S.v[k]) * ld_cg(out + S.ci[k]);
+            out[pi] = with_diag ? acc / pd : acc;
+            // further rows of this level owned by this thread (levels wider than the grid)
+            const int e = S.dlev[l + 1];
+            for (int t = pt + nthr; t < e; t += nthr) {
+                const int i = S.rows[t];
+                T a2 = in_coherent ? ld_cg(in + i) : in[i];
+                const int k1 = S.rp[t + 1];
+                for (int k = S.rp[t]; k < k1; ++k) a2 -= val_as<T, V>(S.v[k]) * ld_cg(out + S.ci[k]);
+                out[i] = with_diag ? a2 / S.d[t] : a2;
+            }
+        }
+        prefetch(l + 1);
+        if (l + 1 < S.nlev || last_barrier) grid_barrier(bar, err);
+    }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) k_sweep_pair(SweepView<T, V> F, int f_diag, SweepView<T, V> B, int b_diag,
+                                                    const T *in, T *y, T *out, unsigned int *bar, int *err) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    sweep_phase<T, V>(F, f_diag, in, false, y, bar, err, tid, nthr, true);
+    sweep_phase<T, V>(B, b_diag, y, true, out, bar, err, tid, nthr, false);
+}
+
+template <typename T, typename V>
+void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
+                     T *y, T *out, unsigned int *bar, int *err, cudaStream_t s) {
+    static int grid = 0;
+    if (!grid) {
+        int per_sm = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_pair<T, V>, 256, 0));
+        grid = sm_count() * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
+    }
+    int maxw = 0;
+    for (int l = 0; l < F.nlev; ++l) maxw = max(maxw, F.lev_ptr[l + 1] - F.lev_ptr[l]);
+    for (int l = 0; l < B.nlev; ++l) maxw = max(maxw, B.lev_ptr[l + 1] - B.lev_ptr[l]);
+    int g = (maxw + 255) / 256;
+    if (g > grid) g = grid;
+    if (g < 1) g = 1;
+    SweepView<T, V> f = F, b = B;
+    void *args[] = {&f, (void *)&f_diag, &b, (void *)&b_diag, (void *)&in, (void *)&y, (void *)&out, (void *)&bar,
+                    (void *)&err};
+    CU(cudaLaunchCooperativeKernel((const void *)k_sweep_pair<T, V>, dim3(g), dim3(256), args, 0, s));
+    count_launch();
+}
+template void sweep_pair_coop<double, double>(const SweepView<double, double> &, int, const SweepView<double, double> &,
+                                              int, const double *, double *, double *, unsigned int *, int *, cudaStream_t);
+template void sweep_pair_coop<float, float>(const SweepView<float, float> &, int, const SweepView<float, float> &, int,
+                                            const float *, float *, float *, unsigned int *, int *, cudaStream_t);
+template void sweep_pair_coop<float, __nv_bfloat16>(const SweepView<float, __nv_bfloat16> &, int,
+                                                    const SweepView<float, __nv_bfloat16> &, int, const float *, float *,
+                                                    float *, unsigned int *, int *, cudaStream_t);
 template void sweep<float, float>(const SweepView<float, float> &, const float *, float *, int, cudaStream_t);
 template void sweep<float, __nv_bfloat16>(const SweepView<float, __nv_bfloat16> &, const float *, float *, int, cudaStream_t);
 
@@ -251,9 +394,10 @@ __device__ void final_reduce(const double *partials, int K, int kmax, double *ou
 constexpr int RT = 256;   // threads per reduction block
 
 // h[k] = (w, V_k) for k < K   (first CGS pass)
-__global__ void __launch_bounds__(RT) k_mdot(size_t n, int K, const double *__restrict__ w,
+__global__ void __launch_bounds__(RT) k_mdot(size_t n, const FgState *st, const double *__restrict__ w,
                                              const double *__restrict__ V, size_t ldv, double *partials,
                                              unsigned int *ticket, double *h) {
+    const int K = st->j + 1;
     double acc[KMAX1];
 #pragma unroll
     for (int k = 0; k < KMAX1; ++k) acc[k] = 0.0;
@@ -272,9 +416,11 @@ __global__ void __launch_bounds__(RT) k_mdot(size_t n, int K, const double *__re
 
 // w -= sum_k hin[k] V_k; then hout[k] = (w, V_k) (second CGS pass) or, with
 // K2 == 0, hout[0] = (w, w).
-__global__ void __launch_bounds__(RT) k_cgs_update(size_t n, int K, const double *__restrict__ hin, double *w,
-                                                   const double *__restrict__ V, size_t ldv, int want_dots,
-                                                   double *partials, unsigned int *ticket, double *hout) {
+__global__ void __launch_bounds__(RT) k_cgs_update(size_t n, const FgState *st, const double *__restrict__ hin,
+                                                   double *w, const double *__restrict__ V, size_t ldv,
+                                                   int want_dots, double *partials, unsigned int *ticket,
+                                                   double *hout) {
+    const int K = st->j + 1;
     __shared__ double hs[KMAX1];
     for (int k = threadIdx.x; k < KMAX1; k += RT) hs[k] = k < K ? hin[k] : 0.0;
     __syncthreads();
@@ -306,9 +452,11 @@ __global__ void __launch_bounds__(RT) k_cgs_update(size_t n, int K, const double
 
 // Givens step for column j (single thread): H column from h1 + h2 and ||w||,
 // apply previous rotations, new rotation, residual estimate.
-__global__ void k_givens(FgState *st, int j) {
+__global__ void k_givens(FgState *st) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (st->stop) return;
     const int m = st->m;
+    const int j = st->j;
     double *H = st->H;                       // H[k*m + j]
     for (int k = 0; k <= j; ++k) H[k * m + j] = st->h1[k] + st->h2[k];
     const double hn = sqrt(st->nrm2[0]);
@@ -336,16 +484,48 @@ __global__ void k_givens(FgState *st, int j) {
     const double est = fabs(st->s[j + 1]) / st->bnorm;
     if (st->hist_len < st->hist_cap) st->hist[st->hist_len++] = est;
     st->jdone = j + 1;
+    st->j = j + 1;
     if (!isfinite(est)) { st->status = 6; st->stop = 1; return; }
-    if (est <= st->tol || hn == 0.0 || st->total >= st->maxit) st->stop = 1;
+    if (est <= st->tol || hn == 0.0 || st->total >= st->maxit || j + 1 >= m) st->stop = 1;
 }
 
-// V_{j+1} = w * inv_hn
-__global__ void k_scale_next(size_t n, const double *__restrict__ w, double *__restrict__ vout, const FgState *st) {
+// V_{j} = w * inv_hn after the Givens step advanced j (skipped at the last column)
+__global__ void k_scale_next(size_t n, const double *__restrict__ w, double *__restrict__ V, const FgState *st) {
+    const int j = st->j;
+    if (j > st->m) return;
+    double *vout = V + (size_t)j * n;
     const double a = st->inv_hn;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         vout[i] = w[i] * a;
 }
+
+template <typename T>
+__global__ void k_load_vj(size_t n, const FgState *st, const double *__restrict__ V, T *__restrict__ zin) {
+    const double *vj = V + (size_t)st->j * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        zin[i] = (T)vj[i];
+}
+template <typename T>
+void load_vj(size_t n, const FgState *st, const double *V, T *zin, cudaStream_t s) {
+    k_load_vj<T><<<grid_for(n, 256), 256, 0, s>>>(n, st, V, zin);
+    CU_LAUNCH("k_load_vj"); count_launch();
+}
+template void load_vj<double>(size_t, const FgState *, const double *, double *, cudaStream_t);
+template void load_vj<float>(size_t, const FgState *, const double *, float *, cudaStream_t);
+
+template <typename T>
+__global__ void k_store_zj(size_t n, const FgState *st, const T *__restrict__ zout, T *__restrict__ Z) {
+    T *zj = Z + (size_t)st->j * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        zj[i] = zout[i];
+}
+template <typename T>
+void store_zj(size_t n, const FgState *st, const T *zout, T *Z, cudaStream_t s) {
+    k_store_zj<T><<<grid_for(n, 256), 256, 0, s>>>(n, st, zout, Z);
+    CU_LAUNCH("k_store_zj"); count_launch();
+}
+template void store_zj<double>(size_t, const FgState *, const double *, double *, cudaStream_t);
+template void store_zj<float>(size_t, const FgState *, const float *, float *, cudaStream_t);
 
 // y = H(1:j,1:j)^{-1} s(1:j) (single thread)
 __global__ void k_backsolve(FgState *st) {
@@ -393,26 +573,26 @@ __global__ void __launch_bounds__(RT) k_norm2(size_t n, const double *__restrict
 
 int reduce_grid() { return sm_count() * 2; }
 
-void mdot(size_t n, int K, const double *w, const double *V, size_t ldv, double *partials, unsigned int *ticket,
-          double *h, cudaStream_t s) {
-    k_mdot<<<reduce_grid(), RT, 0, s>>>(n, K, w, V, ldv, partials, ticket, h);
+void mdot(size_t n, const FgState *st, const double *w, const double *V, size_t ldv, double *partials,
+          unsigned int *ticket, double *h, cudaStream_t s) {
+    k_mdot<<<reduce_grid(), RT, 0, s>>>(n, st, w, V, ldv, partials, ticket, h);
     CU_LAUNCH("k_mdot"); count_launch();
 }
-void cgs_update(size_t n, int K, const double *hin, double *w, const double *V, size_t ldv, int want_dots,
-                double *partials, unsigned int *ticket, double *hout, cudaStream_t s) {
-    k_cgs_update<<<reduce_grid(), RT, 0, s>>>(n, K, hin, w, V, ldv, want_dots, partials, ticket, hout);
+void cgs_update(size_t n, const FgState *st, const double *hin, double *w, const double *V, size_t ldv,
+                int want_dots, double *partials, unsigned int *ticket, double *hout, cudaStream_t s) {
+    k_cgs_update<<<reduce_grid(), RT, 0, s>>>(n, st, hin, w, V, ldv, want_dots, partials, ticket, hout);
     CU_LAUNCH("k_cgs_update"); count_launch();
 }
 void norm2(size_t n, const double *v, double *partials, unsigned int *ticket, double *out, cudaStream_t s) {
     k_norm2<<<reduce_grid(), RT, 0, s>>>(n, v, partials, ticket, out);
     CU_LAUNCH("k_norm2"); count_launch();
 }
-void givens(FgState *st, int j, cudaStream_t s) {
-    k_givens<<<1, 32, 0, s>>>(st, j);
+void givens(FgState *st, cudaStream_t s) {
+    k_givens<<<1, 32, 0, s>>>(st);
     CU_LAUNCH("k_givens"); count_launch();
 }
-void scale_next(size_t n, const double *w, double *vout, const FgState *st, cudaStream_t s) {
-    k_scale_next<<<grid_for(n, 256), 256, 0, s>>>(n, w, vout, st);
+void scale_next(size_t n, const double *w, double *V, const FgState *st, cudaStream_t s) {
+    k_scale_next<<<grid_for(n, 256), 256, 0, s>>>(n, w, V, st);
     CU_LAUNCH("k_scale_next"); count_launch();
 }
 void backsolve(FgState *st, cudaStream_t s) {
@@ -430,6 +610,7 @@ __global__ void k_restart_scale(size_t n, const double *__restrict__ r, double *
         for (int k = 0; k <= st->m; ++k) st->s[k] = 0.0;
         st->s[0] = beta;
         st->jdone = 0;
+        st->j = 0;
         st->stop = 0;
     }
 }

@@ -14,6 +14,7 @@ constexpr int KMAX1 = 32;
 // round trip except the stop flag.
 struct FgState {
     int m, maxit, total, hist_len, hist_cap, jdone, stop, status;
+    int j, pad_i;                           // current inner column
     double tol, bnorm, inv_hn, pad;
     double H[(KMAX1 + 1) * KMAX1];
     double cs[KMAX1], sn[KMAX1], s[KMAX1 + 1], y[KMAX1];
@@ -34,6 +35,7 @@ template <typename T, typename V>
 struct SweepView {
     int nlev;
     const int *lev_ptr;   // host
+    const int *dlev;      // device copy
     const int *rows, *rp, *ci;
     const V *v;
     const T *d;           // diagonal per schedule position (or nullptr)
@@ -48,6 +50,13 @@ template <typename T, typename V>
 void level_residual(const LevelMats<V> &M, const T *x, const T *b, T *r, cudaStream_t s);
 template <typename T, typename V>
 void sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag, cudaStream_t s);
+// Both triangular solves of one smoother application in one cooperative
+// launch: y = F^{-1} in (schedule levels of F), out = B^{-1} y, with a
+// bounded grid barrier between levels.  bar: 2 device words (zeroed), err:
+// device word set when a barrier wait gives up.
+template <typename T, typename V>
+void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
+                     T *y, T *out, unsigned int *bar, int *err, cudaStream_t s);
 template <typename T>
 void restrict_to(int nc, const int *mptr, const int *midx, const T *r, T *h, cudaStream_t s);
 template <typename T, typename Q>
@@ -59,12 +68,19 @@ void convert_f32_f64(size_t n, const float *in, double *out, cudaStream_t s);
 template <typename T>
 void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, cudaStream_t s);
 
-void mdot(size_t n, int K, const double *w, const double *V, size_t ldv, double *partials, unsigned int *ticket,
-          double *h, cudaStream_t s);
-void cgs_update(size_t n, int K, const double *hin, double *w, const double *V, size_t ldv, int want_dots,
-                double *partials, unsigned int *ticket, double *hout, cudaStream_t s);
+// K = st->j + 1 basis vectors (read on the device)
+void mdot(size_t n, const FgState *st, const double *w, const double *V, size_t ldv, double *partials,
+          unsigned int *ticket, double *h, cudaStream_t s);
+void cgs_update(size_t n, const FgState *st, const double *hin, double *w, const double *V, size_t ldv,
+                int want_dots, double *partials, unsigned int *ticket, double *hout, cudaStream_t s);
+// zin = V_{st->j} (FP64 copy or FP32 conversion)
+template <typename T>
+void load_vj(size_t n, const FgState *st, const double *V, T *zin, cudaStream_t s);
+// Z_{st->j} = zout
+template <typename T>
+void store_zj(size_t n, const FgState *st, const T *zout, T *Z, cudaStream_t s);
 void norm2(size_t n, const double *v, double *partials, unsigned int *ticket, double *out, cudaStream_t s);
-void givens(FgState *st, int j, cudaStream_t s);
+void givens(FgState *st, cudaStream_t s);
 void scale_next(size_t n, const double *w, double *vout, const FgState *st, cudaStream_t s);
 void backsolve(FgState *st, cudaStream_t s);
 template <typename ZT>

@@ -9,9 +9,9 @@ Matching (aggregation by graph matching, Section 2):
   key multiset, sorted in decreasing order, is lexicographically largest;
 * the weight of a structurally one-sided entry is |a_uv|/2; A and A^T give
   the same matching.
-Aggregates (eq. (3) and the part map of Section 2): a partition; P*1 = 1;
+Aggregates (eq. (4) and the part map of Section 2): a partition; P*1 = 1;
 rank P = N_c (Theorem 1); size <= 2^passes; ids ordered by smallest member.
-Galerkin (eq. (1) and its entrywise form, Section 2): brute-force dense
+Galerkin (eq. (3) and its entrywise form, Section 2): brute-force dense
 P^T A P on dyadic values (exact); row sums A_c 1 = P^T A 1; symmetric ->
 symmetric; SPD -> SPD (Theorem 2); diagonally dominant M-matrix -> the same
 (Theorem of Kim et al. quoted in Section 2.1); the 4x4 counterexample of

@@ -11,7 +11,7 @@ Section 3):
   a breakdown;
 * for a symmetric M-matrix the ILU iteration converges (Theorem of Meijerink
   and van der Vorst quoted in Section 2.1): rho(I - S^{-1}A) < 1.
-Preconditioner (eq. (4), Algorithm 1 SOLVE B~q = z):
+Preconditioner (eq. (5), Algorithm 1 SOLVE B~q = z):
 * equals the paper's three-solve form t + f - q';
 * with an exact coarse solve, (I - M^{-1}A) P = 0 (Theorem 1);
 * the Richardson coarse solve equals sum_{k<m} (I - B^{-1}A)^k B^{-1};
