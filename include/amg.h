@@ -181,6 +181,22 @@ int amg_precond_apply(amg_handle_t *h, const double *z, double *q, int32_t trans
  * device [n].  Stream-ordered on `stream`; does not synchronise. */
 int amg_spmv(const amg_csr_t *A, const double *x, double *y, void *stream);
 
+/* y = A x like amg_spmv, for callers that must not let the library allocate
+ * device memory (for example code capturing a CUDA graph on `stream`, or
+ * code that owns a fixed memory budget): the int32 row-pointer copy that
+ * amg_spmv allocates per call lives instead in a fixed file-scope device
+ * array of AMG_NOALLOC_MAX_ROWS + 1 entries plus a status word (16 MiB +
+ * 512 B), held by every GPU that loads the library until the process exits.
+ * The paper has no counterpart: this is an interface variant only.
+ * Pointers as in amg_spmv (device).  The first call on a device looks up the
+ * array's address with that device current; make that first call before any
+ * stream capture.  Every call shares the array, so calls that overlap on the
+ * GPU race: serialise them on one stream.  Synchronises `stream`.  Errors:
+ * AMG_ERR_INVALID_ARG for n > AMG_NOALLOC_MAX_ROWS, nnz >= 2^31, null
+ * pointers or invalid row pointers; AMG_ERR_CUDA. */
+#define AMG_NOALLOC_MAX_ROWS 4194304
+int amg_spmv_noalloc(const amg_csr_t *A, const double *x, double *y, void *stream);
+
 /* ------------------------------------------------------- introspection */
 /* Level l facts: info[0] rows, [1] stored entries, [2] sweep levels of the
  * forward ILU(0) solve (colours in colour order), [3] 1 if dense final

@@ -16,7 +16,7 @@ from typing import Optional
 import numpy as np
 
 from . import _lib
-from ._lib import (AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
+from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
                    AMG_ERR_CUDA, AMG_ERR_INVALID_ARG, AMG_ERR_LIMIT, AMG_ERR_NOT_CONVERGED,
                    AMG_ERR_NOT_SUPPORTED, AMG_ERR_NUMERIC, AMG_ERR_OOM, AMG_FP32, AMG_FP64, AMG_OK,
                    AMG_ORDER_COLOR, AMG_ORDER_NATURAL, AmgCsr, AmgOptions, AmgStats)
@@ -27,7 +27,7 @@ __all__ = [
     "amg_num_levels", "amg_get_aggregates", "amg_get_matrix", "amg_get_pass_matrix",
     "amg_get_colors", "amg_get_ilu", "amg_fv_assemble", "amg_fv_grad_logk", "amg_version",
     "amg_status_string", "lib", "amg_set_kernel_timing", "amg_get_kernel_timing",
-    "amg_launch_counter", "amg_csr_value_grad",
+    "amg_launch_counter", "amg_csr_value_grad", "amg_spmv_noalloc",
 ]
 
 
@@ -188,6 +188,17 @@ def amg_spmv(A, x, y, stream=None):
     if stream is None:
         stream = _stream_of(x)
     _check(lib().amg_spmv(C.byref(cs), _ptr(x, "float64"), _ptr(y, "float64"), stream), "amg_spmv")
+
+
+def amg_spmv_noalloc(A, x, y, stream=None):
+    """amg_spmv without any device allocation: its scratch is a fixed device
+    array shared by all calls (at most AMG_NOALLOC_MAX_ROWS rows; calls that
+    overlap on the GPU race on it)."""
+    cs = _csr(A)
+    if stream is None:
+        stream = _stream_of(x)
+    _check(lib().amg_spmv_noalloc(C.byref(cs), _ptr(x, "float64"), _ptr(y, "float64"), stream),
+           "amg_spmv_noalloc")
 
 
 def amg_set_kernel_timing(h: Handle, kclass: int):

@@ -23,6 +23,7 @@ AMG_ERR_NOT_CONVERGED = 7
 AMG_ERR_LIMIT = 8
 
 AMG_FP64, AMG_FP32, AMG_BF16 = 0, 1, 2
+AMG_NOALLOC_MAX_ROWS = 4194304
 AMG_ORDER_COLOR, AMG_ORDER_NATURAL = 0, 1
 AMG_COLOR_HASH_JP, AMG_COLOR_FIRST_FIT = 0, 1
 
@@ -67,6 +68,7 @@ SIGNATURES = {
     "amg_get_history": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int32)]),
     "amg_precond_apply": (C.c_int, [_P, _P, _P, C.c_int32]),
     "amg_spmv": (C.c_int, [C.POINTER(AmgCsr), _P, _P, _P]),
+    "amg_spmv_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, _P, _P]),
     "amg_get_level_info": (C.c_int, [_P, C.c_int32, _P]),
     "amg_num_levels": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "amg_get_aggregates": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),

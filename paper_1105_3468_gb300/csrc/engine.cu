@@ -735,6 +735,13 @@ static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, a
 
 }  // namespace amg
 
+// Lets the other translation units of the ABI report a message through
+// amg_last_error().
+const char *amg_noalloc_set_error(const char *msg) {
+    amg::t_last_error = msg;
+    return amg::t_last_error.c_str();
+}
+
 // =================================================================== C ABI
 using namespace amg;
 
