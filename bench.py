@@ -50,7 +50,102 @@ def workload(name):
     if name == "c1":
         return (W.c1_block_2d_64(), 1e-8, 600, {},
                 "fv2d-64^2-blockkappa (4096 unknowns), FGMRES(30), tol 1e-8")
+    if name == "c5":
+        return (W.c5_batch_specs(), 1e-8, 600, {},
+                "batch of 64 uneven systems: 48 block-kappa grids side U{64..512} + 16 random-geometric-graph "
+                "matrices 10k..500k rows, 7..30 nnz/row (8.8 M rows); one solve loop, FP64 FGMRES(30), tol 1e-8")
     raise ValueError(name)
+
+
+def batch_members(specs, amg, on_device=True):
+    """Matrices (device CSR) and right-hand sides of the batch recipe."""
+    import numpy as np
+    from paper_1105_3468_gb300 import workloads as W
+    mats, rhs = [], []
+    for sp in specs:
+        if sp.kind == "grid":
+            A, _ = amg.assemble_fv(W.batch_grid_problem(sp))
+        else:
+            A = amg.CsrDevice.from_host(W.rgg_matrix(sp.size, sp.nnz_per_row, sp.seed))
+        mats.append(A)
+        rhs.append(W.batch_rhs(sp, A.n))
+    return mats, np.concatenate(rhs)
+
+
+def run_batch(args, amg, torch):
+    """Batched path: setup + solve of the 64-system batch per step.  Under
+    torchrun the members are split across ranks (longest-processing-time
+    first by nonzeros, no data-path collective); the step time is the
+    slowest rank's, so `value` is the time for the whole batch."""
+    import torch.distributed as dist
+    from paper_1105_3468_gb300 import shard
+    rank, world, local = dist_env()
+    specs, tol, maxit, sopts, desc = workload("c5")
+    parts = shard.lpt_partition([shard.member_weight(s) for s in specs], world)
+    mine = [specs[k] for k in parts[rank]]
+    mats, rhs = batch_members(mine, amg)
+    b = torch.tensor(rhs, device="cuda")
+    vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
+    rows = sum(A.n for A in mats)
+    nnz = sum(A.nnz for A in mats)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(prec):
+        h = amg.amg_setup_batched(mats, vcycle_prec=prec, maxit=maxit)
+        x = torch.zeros_like(b)
+        st = amg.amg_solve_batched(h, b, x, tol)
+        h.close()
+        return st
+
+    for _ in range(args.warmup):
+        step(vp)
+    res = {}
+    for prec in (vp, amg.AMG_FP64) if vp != amg.AMG_FP64 else (vp,):
+        barrier()
+        torch.cuda.synchronize()
+        l0 = amg.amg_launch_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            st = step(prec)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        res[prec] = (ms, st, amg.amg_launch_counter() - l0)
+    ms, st, launches = res[vp]
+    summary = ([(s.iters, s.status) for s in st], rows, nnz, launches)
+    if world > 1:
+        got = [None] * world
+        dist.all_gather_object(got, summary)
+    else:
+        got = [summary]
+    if rank != 0:
+        return
+    per_member = shard.merge(parts, [g[0] for g in got])
+    rows = sum(g[1] for g in got)
+    nnz = sum(g[2] for g in got)
+    launches = sum(g[3] for g in got)
+    out = {"metric": "batch time-to-rel-residual 1e-8 (64 uneven systems)", "value": round(ms, 2), "unit": "ms",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
+           "higher_is_better": False, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+           "dtype": {"fp32": "f32 V-cycle / f64 FGMRES", "bf16": "bf16 values, f32 V-cycle / f64 FGMRES",
+                     "fp64": "f64"}[args.prec], "data": "synthetic",
+           "config": {"workload": desc, "rows": rows, "nnz": nnz,
+                      "parallelism": f"members split over {world} ranks (LPT by nnz)" if world > 1 else "single GPU"},
+           "rows_per_s": round(rows / (ms * 1e-3)),
+           "iters_min_max": [min(i for i, _ in per_member), max(i for i, _ in per_member)],
+           "all_converged": all(s == 0 for _, s in per_member), "gpu_launches": int(launches)}
+    if amg.AMG_FP64 in res and vp != amg.AMG_FP64:
+        out["fp64_ms_per_step"] = round(res[amg.AMG_FP64][0], 2)
+    print(json.dumps(out), flush=True)
 
 
 class ClockSampler:
@@ -174,15 +269,19 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c5"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp64"])
-    ap.add_argument("--roofline-class", type=int, default=1)
+    ap.add_argument("--roofline-class", type=int, default=2,
+                    help="kernel class timed live for the roofline: 1 outer SpMV, 2 ILU(0) smoother, 3 CGS2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--maxit", type=int, default=None, help="override the workload's iteration cap")
     ap.add_argument("--profile-run", action="store_true",
                     help="one setup + solve of the workload (for ncu captures), no timing output")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2],
+                    help="ILU(0) sweep schedule: 0 per-level launches, 1 level barriers, 2 dataflow")
+    ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
     ap.add_argument("--steps-ref", type=int, default=2)
     ap.add_argument("--warmup-ref", type=int, default=0)
     args = ap.parse_args()
@@ -201,6 +300,8 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
+    if args.workload == "c5":
+        return run_batch(args, amg, torch)
 
     def barrier():
         if world > 1:
@@ -213,6 +314,9 @@ def main():
     torch.cuda.synchronize()
     vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
     opts = dict(sopts, maxit=maxit)
+    for k in ("persistent", "orthog"):
+        if getattr(args, k) is not None:
+            opts[k] = getattr(args, k)
 
     def step(prec, timing_class=0, acc=None):
         h = amg.amg_setup(A, vcycle_prec=prec, **opts)
@@ -258,8 +362,8 @@ def main():
     with ClockSampler(local) as clk:
         ms, stats, acc, launches = timed(vp, args.roofline_class)
     clocks = clk.summary()
-    ms64, stats64, _, _ = (timed(amg.AMG_FP64, steps=args.fp64_steps) if vp != amg.AMG_FP64
-                           else (ms, stats, None, None))
+    ms64, stats64, acc64, _ = (timed(amg.AMG_FP64, timing_class=1, steps=args.fp64_steps) if vp != amg.AMG_FP64
+                               else (ms, stats, [], None))
 
     # end to end through the C ABI with host buffers (copies inside the region)
     Ah = amg.CsrDevice(A.n, A.row_ptr.cpu().numpy(), A.col.cpu().numpy(), A.val.cpu().numpy())
@@ -283,12 +387,23 @@ def main():
     roof = None
     if tot_n:
         achieved = tot_b / tot_n / (tot_ms / tot_n * 1e-3) / 1e9
-        names = {1: "outer FP64 SpMV w = A z_j", 2: "level-0 ILU(0) sweeps", 3: "CGS2 pass"}
+        names = {1: "outer FP64 SpMV w = A z_j", 2: "ILU(0) smoother applications, all levels (k_sweep_pair/k_sweep)",
+                 3: "CGS2 pass"}
         roof = {"bound": "hbm", "kernel": names.get(args.roofline_class), "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": "measured" if peaks else "fallback", "unit": "GB/s",
                 "frac": round(achieved / peak, 3), "traffic": None,
                 "bytes_per_launch": round(tot_b / tot_n), "avg_launch_us": round(1e3 * tot_ms / tot_n, 2),
                 "launches": tot_n}
+    spmv_roof = None
+    if acc64:
+        n1 = sum(a[1] for a in acc64)
+        if n1:
+            ms1, b1 = sum(a[0] for a in acc64), sum(a[2] for a in acc64)
+            ach = b1 / (ms1 * 1e-3) / 1e9
+            spmv_roof = {"bound": "hbm", "kernel": "outer FP64 SpMV w = A z_j (FP64 V-cycle run)",
+                         "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 3),
+                         "bytes_per_launch": round(b1 / n1), "avg_launch_us": round(1e3 * ms1 / n1, 2),
+                         "launches": n1}
     s0 = stats[-1]
     out = {
         "metric": METRIC, "value": round(ms, 2), "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -296,14 +411,14 @@ def main():
         "vs_baseline": None, "dtype": {"fp32": "f32 V-cycle / f64 FGMRES", "bf16": "bf16 values, f32 V-cycle / f64 FGMRES",
                                        "fp64": "f64"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": desc, "l2": "inputs larger than L2 (matrix 175 MB)",
+        "config": {"workload": desc, "l2": "inputs larger than L2 (matrix 175 MB)", "options": opts,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iters": s0.iters, "rel_res_true": s0.rel_res_true, "setup_ms": round(s0.setup_ms, 2),
         "solve_ms": round(s0.solve_ms, 2), "fp64_ms_per_step": round(ms64, 2), "fp64_iters": stats64[-1].iters,
         "speedup_vs_fp64": round(ms64 / ms, 3), "levels": s0.nlevels,
         "e2e": {"value": round(statistics.median(e2e), 2), "unit": "ms", "h2d_bytes_per_step": int(bi),
                 "d2h_bytes_per_step": int(bo)},
-        "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+        "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "spmv_roofline": spmv_roof,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob, tol, stats64[-1].iters, sopts)

@@ -75,6 +75,10 @@ extern "C" {
 #define AMG_COLOR_HASH_JP 0     /* priority (mix64(i ^ (seed + 0x9e3779b97f4a7c15)), i) */
 #define AMG_COLOR_FIRST_FIT 1   /* priority -i (first fit in index order)  */
 
+/* Orthogonalisation of the outer FGMRES (Arnoldi process). */
+#define AMG_ORTHO_MGS 0         /* modified Gram-Schmidt                   */
+#define AMG_ORTHO_CGS2 1        /* classical Gram-Schmidt, two passes      */
+
 typedef struct amg_handle amg_handle_t;
 
 /* A square sparse matrix in CSR form (Section 1: A in R^{N x N}). */
@@ -107,10 +111,27 @@ typedef struct {
     int32_t build_adjoint;    /* nonzero: also build transposed structures */
     int32_t use_graphs;       /* nonzero: replay the inner iteration as a CUDA
                                  graph captured once per handle: 1          */
-    int32_t persistent;       /* nonzero: each ILU(0) smoother application
-                                 is one cooperative kernel with a bounded
-                                 grid barrier between schedule levels; a
-                                 wait that gives up returns AMG_ERR_LIMIT: 1 */
+    int32_t persistent;       /* ILU(0) smoother schedule.  0: one launch per
+                                 schedule level.  1: an application with
+                                 more than 16 schedule levels (forward +
+                                 backward) is one cooperative kernel with a
+                                 bounded grid barrier between levels.  2:
+                                 every application is one cooperative
+                                 kernel in which each row starts when the
+                                 rows it reads are written (no level
+                                 barriers; bounded waits).  All three give
+                                 bit-identical results.  A wait that gives
+                                 up returns AMG_ERR_LIMIT.  Default: 1      */
+    int32_t deep_block_max;   /* levels >= 2 with at most this many rows (and
+                                 all levels below them) run their V-cycle in
+                                 one thread block when deep_inner == 1;
+                                 0 disables (default: measured slower)      */
+    int32_t orthog;           /* Arnoldi orthogonalisation of the outer
+                                 FGMRES: AMG_ORTHO_MGS (modified Gram-
+                                 Schmidt, one cooperative kernel per
+                                 column) or AMG_ORTHO_CGS2 (classical
+                                 Gram-Schmidt with one re-orthogonalisation
+                                 pass): AMG_ORTHO_MGS                      */
     uint64_t seed;            /* tie-break seed, default 0                 */
 } amg_options_t;
 
@@ -166,6 +187,33 @@ int amg_solve(amg_handle_t *h, const double *b, double *x, double tol, amg_stats
  * Needs build_adjoint.  g, lambda: host or device [n]; lambda is read as
  * the initial guess.  Errors as amg_solve. */
 int amg_adjoint(amg_handle_t *h, const double *g, double *lambda, double tol, amg_stats_t *stats);
+
+/* ------------------------------------------------------------- batches */
+/* Sets up `count` independent systems (the batched path): one hierarchy per
+ * system, built concurrently from a few host threads, each system on its own
+ * internal stream.  The per-system results are those amg_setup gives for
+ * that system alone.  systems: host array of `count` CSR descriptors (their
+ * arrays host or device).  Errors as amg_setup, the message naming the
+ * first failing system; nothing is kept on error. */
+int amg_setup_batched(const amg_csr_t *systems, int32_t count, const amg_options_t *opt, void *stream,
+                      amg_handle_t **out);
+/* Solves every system of a batched handle: b_cat and x_cat (host or device)
+ * hold the systems' vectors back to back, at the offsets amg_batch_size
+ * reports.  One host loop advances all systems: each active system queues
+ * one FGMRES inner iteration (a CUDA graph replay on its stream, so the
+ * systems run concurrently), then each is collected; a system that has
+ * converged or failed drops out.  per_system (host, may be NULL) receives
+ * `count` stats.  Returns the first error, else AMG_ERR_NOT_CONVERGED if any
+ * system hit maxit, else AMG_OK.  Each system's iterates are exactly those
+ * of amg_solve on that system alone. */
+int amg_solve_batched(amg_handle_t *h, const double *b_cat, double *x_cat, double tol,
+                      amg_stats_t *per_system);
+/* Number of systems and their row offsets (host, count + 1 entries; may be
+ * NULL) of a batched handle; count = 0 for a single-system handle. */
+int amg_batch_size(amg_handle_t *h, int32_t *count, int64_t *offsets);
+/* The handle of system k of a batch (owned by the batch; for introspection
+ * calls such as amg_get_history), or NULL. */
+amg_handle_t *amg_batch_member(amg_handle_t *h, int32_t k);
 
 /* Residual history of the last solve or adjoint call: entry 0 is
  * ||r0||/||b||, then one FGMRES estimate |s_{j+1}|/||b|| per inner

@@ -267,7 +267,7 @@ class Options(NamedTuple):
     passes: int = 2           # matching passes per level (aggregates <= 2^passes)
     coarse_inner: int = 5     # Richardson steps of the level-1 coarse solve
     deep_inner: int = 1       # Richardson steps on deeper levels
-    dense_max: int = 1024     # a level this small is solved by dense LU
+    dense_max: int = 1024     # a level this small is solved exactly (dense inverse)
     max_levels: int = 12
     order_fine: int = ORDER_NATURAL
     order_coarse: int = ORDER_COLOR
@@ -350,7 +350,7 @@ class Hierarchy:
         return out
 
     def level_solve(self, l: int, h, transpose=False):
-        """C_l(h): the inexact solve of level l >= 1 (dense LU on the last level)."""
+        """C_l(h): the inexact solve of level l >= 1 (dense inverse on the last level)."""
         out = np.zeros(self.levels[l]["n"])
         lib().or_level_solve(self._h, l, _f64(h), out, int(transpose))
         return out

@@ -583,60 +583,54 @@ void or_ilu_solve_t(int n, const int64_t *rp, const int32_t *ci, const double *l
 }
 
 /* ------------------------------------------------------------------ */
-/* Dense LU with partial pivoting (row interchanges), used for the      */
-/* exact solve on the smallest level.  a is n x n row-major, in place.  */
+/* Exact solve of the smallest level: the inverse by Gauss-Jordan        */
+/* elimination with partial pivoting on [A | I] (pivot of column k: the  */
+/* first row of largest magnitude at or below k; the pivot row is        */
+/* divided by the pivot, then each other row i with f = m_ik != 0 gets   */
+/* m_ij - f m_kj), applied as a product with the inverse, rows summed in */
+/* column order.  a is n x n row-major (input); inv receives A^{-1}.     */
 /* ------------------------------------------------------------------ */
-static int dense_lu(int n, double *a, int32_t *piv)
+static int dense_inverse(int n, const double *a, double *inv)
 {
+    size_t w = 2 * (size_t)n;
+    double *m = calloc((size_t)n * w, sizeof(double));
+    double *f = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) m[(size_t)i * w + j] = a[(size_t)i * n + j];
+        m[(size_t)i * w + n + i] = 1.0;
+    }
+    int status = OR_OK;
     for (int k = 0; k < n; ++k) {
         int p = k;
-        double best = fabs(a[(size_t)k * n + k]);
+        double best = fabs(m[(size_t)k * w + k]);
         for (int i = k + 1; i < n; ++i)
-            if (fabs(a[(size_t)i * n + k]) > best) { best = fabs(a[(size_t)i * n + k]); p = i; }
-        piv[k] = p;
-        if (best == 0.0 || !isfinite(best)) return OR_EBREAKDOWN;
+            if (fabs(m[(size_t)i * w + k]) > best) { best = fabs(m[(size_t)i * w + k]); p = i; }
+        if (!(best > 0.0) || !isfinite(best)) { status = OR_EBREAKDOWN; p = k; }
         if (p != k)
-            for (int j = 0; j < n; ++j) {
-                double t = a[(size_t)k * n + j]; a[(size_t)k * n + j] = a[(size_t)p * n + j]; a[(size_t)p * n + j] = t;
+            for (size_t j = 0; j < w; ++j) {
+                double t = m[(size_t)k * w + j]; m[(size_t)k * w + j] = m[(size_t)p * w + j]; m[(size_t)p * w + j] = t;
             }
-        for (int i = k + 1; i < n; ++i) {
-            double l = a[(size_t)i * n + k] / a[(size_t)k * n + k];
-            a[(size_t)i * n + k] = l;
-            for (int j = k + 1; j < n; ++j) a[(size_t)i * n + j] = a[(size_t)i * n + j] - l * a[(size_t)k * n + j];
+        double d = m[(size_t)k * w + k];
+        for (size_t j = 0; j < w; ++j) m[(size_t)k * w + j] = m[(size_t)k * w + j] / d;
+        for (int i = 0; i < n; ++i) f[i] = (i == k) ? 0.0 : m[(size_t)i * w + k];
+        for (int i = 0; i < n; ++i) {
+            if (i == k || f[i] == 0.0) continue;
+            for (size_t j = 0; j < w; ++j) m[(size_t)i * w + j] = m[(size_t)i * w + j] - f[i] * m[(size_t)k * w + j];
         }
     }
-    return OR_OK;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) inv[(size_t)i * n + j] = m[(size_t)i * w + n + j];
+    free(m); free(f);
+    return status;
 }
 
-/* x = A^{-1} b (transpose = 0) or A^{-T} b (transpose = 1) from dense_lu. */
-static void dense_solve(int n, const double *a, const int32_t *piv, const double *b, double *x, int transpose)
+/* x = A^{-1} b (transpose = 0) or A^{-T} b (transpose = 1) from the inverse. */
+static void dense_solve(int n, const double *inv, const double *b, double *x, int transpose)
 {
-    for (int i = 0; i < n; ++i) x[i] = b[i];
-    if (!transpose) {
-        for (int k = 0; k < n; ++k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
-        for (int i = 0; i < n; ++i) {
-            double s = x[i];
-            for (int j = 0; j < i; ++j) s -= a[(size_t)i * n + j] * x[j];
-            x[i] = s;
-        }
-        for (int i = n - 1; i >= 0; --i) {
-            double s = x[i];
-            for (int j = i + 1; j < n; ++j) s -= a[(size_t)i * n + j] * x[j];
-            x[i] = s / a[(size_t)i * n + i];
-        }
-    } else {
-        /* A = P^T L U  =>  A^T = U^T L^T P;  solve U^T y = b, L^T w = y, x = P^T w */
-        for (int i = 0; i < n; ++i) {
-            double s = x[i];
-            for (int j = 0; j < i; ++j) s -= a[(size_t)j * n + i] * x[j];
-            x[i] = s / a[(size_t)i * n + i];
-        }
-        for (int i = n - 1; i >= 0; --i) {
-            double s = x[i];
-            for (int j = i + 1; j < n; ++j) s -= a[(size_t)j * n + i] * x[j];
-            x[i] = s;
-        }
-        for (int k = n - 1; k >= 0; --k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += (transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j]) * b[j];
+        x[i] = s;
     }
 }
 
@@ -647,12 +641,12 @@ static void dense_solve(int n, const double *a, const int32_t *piv, const double
 /* Every non-final level keeps its ILU(0) factors (the smoother S_l of   */
 /* Algorithm 1) in its elimination order: natural (the paper's GMG-NO,   */
 /* Section 3) or colour-major.  Coarsening stops when a level has at     */
-/* most dense_max rows (it is then solved exactly by dense LU), when     */
+/* most dense_max rows (it is then solved exactly, by its inverse), when */
 /* matching no longer shrinks the level by 10%, or at max_levels; a      */
-/* final level too large for dense LU keeps only its ILU(0) factors.     */
+/* final level too large for the inverse keeps only its ILU(0) factors.  */
 /*                                                                       */
-/* Reading of the inexact coarse solve (the paper: one ILUT(A_c) solve;  */
-/* the benchmark spec: a fixed small number of inner iterations): the    */
+/* Reading of the inexact coarse solve (Section 2 applies one ILUT(A_c)  */
+/* solve; here a fixed small number of inner iterations is used): the    */
 /* coarse system of level l+1 is solved by k_{l+1} Richardson steps      */
 /*   g <- g + B_{l+1}^{-1} (h - A_{l+1} g),  g = 0 initially,            */
 /* whose preconditioner B_{l+1} is the same two-grid construction built  */
@@ -675,8 +669,7 @@ typedef struct {
     int32_t *color;                     /* elimination-order labels */
     int ncol;
     double *lu;                         /* ILU(0) factors on A's layout */
-    double *dense;                      /* final level: dense LU, or NULL */
-    int32_t *piv;
+    double *dense;                      /* final level: dense inverse, or NULL */
 } or_level_t;
 
 typedef struct {
@@ -707,7 +700,7 @@ void or_free(or_hier_t *H)
         or_level_t *L = &H->lev[l];
         csr_free(&L->A);
         for (int p = 0; p < OR_MAX_PASSES; ++p) { csr_free(&L->mid[p]); free(L->agg_pass[p]); }
-        free(L->agg); free(L->color); free(L->lu); free(L->dense); free(L->piv);
+        free(L->agg); free(L->color); free(L->lu); free(L->dense);
     }
     free(H);
 }
@@ -779,12 +772,13 @@ or_hier_t *or_setup(int n, const int64_t *rp, const int32_t *ci, const double *v
         }
         int m = L->A.n;
         if (last && m <= dense_max) {
-            L->dense = calloc((size_t)m * (size_t)m, sizeof(double));
-            L->piv = malloc(sizeof(int32_t) * (size_t)m);
+            double *a = calloc((size_t)m * (size_t)m, sizeof(double));
+            L->dense = malloc(sizeof(double) * (size_t)m * (size_t)m);
             for (int i = 0; i < m; ++i)
                 for (int64_t e = L->A.rp[i]; e < L->A.rp[i + 1]; ++e)
-                    L->dense[(size_t)i * m + L->A.ci[e]] = L->A.v[e];
-            if (dense_lu(m, L->dense, L->piv) != OR_OK) *status = OR_EBREAKDOWN;
+                    a[(size_t)i * m + L->A.ci[e]] = L->A.v[e];
+            if (dense_inverse(m, a, L->dense) != OR_OK) *status = OR_EBREAKDOWN;
+            free(a);
         } else {
             int ord = (l == 0) ? order_fine : order_coarse;
             L->color = malloc(sizeof(int32_t) * (size_t)m);
@@ -875,8 +869,8 @@ void or_hier_lu(const or_hier_t *H, int l, double *out)
 /*   h[I] = sum_{i in G_I} r_i        restriction P^T (i ascending)      */
 /*   g = C_{l+1}(h)                   inexact coarse solve               */
 /*   q_i = t_i + g[agg_i]             prolongation P and correction      */
-/* C_m(h): dense LU solve on a dense final level; k_m Richardson steps   */
-/* with S_m^{-1} on a final level without dense LU; otherwise k_m        */
+/* C_m(h): product with the inverse on a dense final level; k_m          */
+/* Richardson steps with S_m^{-1} on a final level without it; else k_m  */
 /* Richardson steps g <- g + B_m^{-1}(h - A_m g) from g = 0.             */
 /* ------------------------------------------------------------------ */
 void or_restrict(const or_hier_t *H, int l, const double *r, double *hc)
@@ -900,7 +894,7 @@ void or_level_solve(const or_hier_t *H, int l, const double *h, double *g, int t
 {
     const or_level_t *L = &H->lev[l];
     int m = L->A.n;
-    if (L->dense) { dense_solve(m, L->dense, L->piv, h, g, transpose); return; }
+    if (L->dense) { dense_solve(m, L->dense, h, g, transpose); return; }
     int k = (l == 1) ? H->coarse_inner : H->deep_inner;
     double *res = malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     double *d = malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));

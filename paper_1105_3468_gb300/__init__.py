@@ -16,7 +16,7 @@ from typing import Optional
 import numpy as np
 
 from . import _lib
-from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
+from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_ORTHO_CGS2, AMG_ORTHO_MGS, AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
                    AMG_ERR_CUDA, AMG_ERR_INVALID_ARG, AMG_ERR_LIMIT, AMG_ERR_NOT_CONVERGED,
                    AMG_ERR_NOT_SUPPORTED, AMG_ERR_NUMERIC, AMG_ERR_OOM, AMG_FP32, AMG_FP64, AMG_OK,
                    AMG_ORDER_COLOR, AMG_ORDER_NATURAL, AmgCsr, AmgOptions, AmgStats)
@@ -27,7 +27,8 @@ __all__ = [
     "amg_num_levels", "amg_get_aggregates", "amg_get_matrix", "amg_get_pass_matrix",
     "amg_get_colors", "amg_get_ilu", "amg_fv_assemble", "amg_fv_grad_logk", "amg_version",
     "amg_status_string", "lib", "amg_set_kernel_timing", "amg_get_kernel_timing",
-    "amg_launch_counter", "amg_csr_value_grad", "amg_spmv_noalloc",
+    "amg_launch_counter", "amg_csr_value_grad", "amg_spmv_noalloc", "amg_setup_batched",
+    "amg_solve_batched", "amg_batch_size", "amg_batch_member",
 ]
 
 
@@ -168,6 +169,47 @@ def amg_adjoint(h: Handle, g, lam, tol: float = 1e-8, allow_not_converged: bool 
     _check(lib().amg_adjoint(h.ptr, _ptr(g, "float64"), _ptr(lam, "float64"), float(tol), C.byref(st)),
            "amg_adjoint", allow)
     return st
+
+
+def amg_setup_batched(systems, opts: Optional[AmgOptions] = None, stream=None, **overrides) -> Handle:
+    """amg_setup_batched: one hierarchy per system (list of CSR objects)."""
+    o = opts if opts is not None else amg_default_options()
+    for k, v in overrides.items():
+        setattr(o, k, int(v))
+    arr = (AmgCsr * len(systems))(*[_csr(A) for A in systems])
+    if stream is None:
+        stream = _stream_of(systems[0].row_ptr)
+    out = C.c_void_p()
+    _check(lib().amg_setup_batched(arr, len(systems), C.byref(o), stream, C.byref(out)), "amg_setup_batched")
+    return Handle(out.value, sum(int(A.n) for A in systems), o, keep=(arr,))
+
+
+def amg_batch_size(h: Handle):
+    """(count, row offsets [count+1]) of a batched handle."""
+    c = C.c_int32(0)
+    _check(lib().amg_batch_size(h.ptr, C.byref(c), None), "amg_batch_size")
+    offs = np.zeros(c.value + 1, np.int64)
+    _check(lib().amg_batch_size(h.ptr, C.byref(c), offs.ctypes.data), "amg_batch_size")
+    return c.value, offs
+
+
+def amg_batch_member(h: Handle, k: int) -> Handle:
+    """Non-owning view of system k's handle (valid while the batch lives)."""
+    p = lib().amg_batch_member(h.ptr, k)
+    if not p:
+        raise IndexError(k)
+    v = Handle(p, 0, h.opts)
+    v.close = lambda: None
+    return v
+
+
+def amg_solve_batched(h: Handle, b_cat, x_cat, tol: float = 1e-8):
+    """amg_solve_batched: returns the per-system stats list."""
+    count, _ = amg_batch_size(h)
+    stats = (AmgStats * count)()
+    _check(lib().amg_solve_batched(h.ptr, _ptr(b_cat, "float64"), _ptr(x_cat, "float64"), float(tol), stats),
+           "amg_solve_batched", (AMG_OK, AMG_ERR_NOT_CONVERGED))
+    return list(stats)
 
 
 def amg_get_history(h: Handle) -> np.ndarray:

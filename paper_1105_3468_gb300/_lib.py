@@ -26,6 +26,7 @@ AMG_FP64, AMG_FP32, AMG_BF16 = 0, 1, 2
 AMG_NOALLOC_MAX_ROWS = 4194304
 AMG_ORDER_COLOR, AMG_ORDER_NATURAL = 0, 1
 AMG_COLOR_HASH_JP, AMG_COLOR_FIRST_FIT = 0, 1
+AMG_ORTHO_MGS, AMG_ORTHO_CGS2 = 0, 1
 
 
 class AmgCsr(C.Structure):
@@ -38,7 +39,8 @@ class AmgOptions(C.Structure):
                 ("dense_max", C.c_int32), ("max_levels", C.c_int32), ("order_fine", C.c_int32),
                 ("order_coarse", C.c_int32), ("coloring", C.c_int32), ("restart", C.c_int32),
                 ("maxit", C.c_int32), ("vcycle_prec", C.c_int32), ("build_adjoint", C.c_int32),
-                ("use_graphs", C.c_int32), ("persistent", C.c_int32), ("seed", C.c_uint64)]
+                ("use_graphs", C.c_int32), ("persistent", C.c_int32), ("deep_block_max", C.c_int32),
+                ("orthog", C.c_int32), ("seed", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,6 +68,10 @@ SIGNATURES = {
     "amg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.POINTER(AmgStats)]),
     "amg_adjoint": (C.c_int, [_P, _P, _P, C.c_double, C.POINTER(AmgStats)]),
     "amg_get_history": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int32)]),
+    "amg_setup_batched": (C.c_int, [_P, C.c_int32, C.POINTER(AmgOptions), _P, C.POINTER(_P)]),
+    "amg_solve_batched": (C.c_int, [_P, _P, _P, C.c_double, _P]),
+    "amg_batch_size": (C.c_int, [_P, C.POINTER(C.c_int32), _P]),
+    "amg_batch_member": (_P, [_P, C.c_int32]),
     "amg_precond_apply": (C.c_int, [_P, _P, _P, C.c_int32]),
     "amg_spmv": (C.c_int, [C.POINTER(AmgCsr), _P, _P, _P]),
     "amg_spmv_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, _P, _P]),

@@ -7,8 +7,10 @@
 #include "../../include/amg.h"
 #include "solve.cuh"
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -46,8 +48,11 @@ struct Level {
     // dense last level
     bool dense = false;
     DBuf<double> inv;
+    // SELL-32 copies for the outer FP64 SpMV (level 0 only)
+    Sell sell, sellT;
     // workspace (vector type of the V-cycle, allocated as bytes)
     DBuf<char> wt, wy, wr, wres, wh, wg, wf;
+    int wy_sent = 0;                      // element size of the sentinel wy holds (dataflow sweeps), 0: none
 };
 
 }  // namespace amg
@@ -74,6 +79,10 @@ struct amg_handle {
     std::vector<double> last_hist;
     double setup_ms = 0.0;
     bool adjoint_ready = false;
+    int deep_first = 1 << 30;             // first level run by the single-block V-cycle
+    std::vector<amg_handle *> subs;       // batch: one handle per system
+    std::vector<int64_t> offs;            // batch: row offsets of the systems [count+1]
+    amg::DBuf<char> deep_desc;            // DeepLevel<T, V>[nlev - deep_first]
     // kernel timing of one kernel class (CUDA events around each launch)
     int tclass = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;
@@ -260,6 +269,9 @@ static void cast_sweep(Sweep &S, int prec, cudaStream_t s) {
     }
 }
 
+template <typename T, typename V>
+static void build_deep(amg_handle *h);
+
 static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
     const amg_options_t &o = h->opt;
     cudaStream_t s = h->stream;
@@ -330,18 +342,31 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
         }
         h->adjoint_ready = true;
     }
+    // SELL-32 copies of A (and A^T) for the outer FP64 products
+    build_sell(h->lev[0]->A, h->lev[0]->A.v.get(), h->lev[0]->sell, s);
+    if (o.build_adjoint) build_sell(h->lev[0]->AT, h->lev[0]->AT.v.get(), h->lev[0]->sellT, s);
     // workspaces
     const size_t tsz = o.vcycle_prec == AMG_FP64 ? sizeof(double) : sizeof(float);
     for (auto &Lp : h->lev) {
         Level &L = *Lp;
         const size_t b = tsz * (size_t)L.A.n;
         L.wt.alloc(b); L.wy.alloc(b); L.wr.alloc(b); L.wres.alloc(b); L.wh.alloc(b); L.wg.alloc(b); L.wf.alloc(b);
+        if (o.persistent == 2) {   // dataflow sweeps expect wy to hold the sentinel on entry
+            if (tsz == sizeof(double)) fill_sentinel<double>(reinterpret_cast<double *>(L.wy.get()), L.A.n, s);
+            else fill_sentinel<float>(reinterpret_cast<float *>(L.wy.get()), L.A.n, s);
+            L.wy_sent = (int)tsz;
+        }
     }
     const size_t n = h->n, m = o.restart;
     h->V.alloc((m + 1) * n);
     if (o.vcycle_prec == AMG_FP64) { h->Zd.alloc(m * n); h->zin64.alloc(n); h->zout64.alloc(n); }
     else { h->Zf.alloc(m * n); h->zin32.alloc(n); h->zout32.alloc(n); }
     CU(cudaMallocHost(&h->hflags, 2 * sizeof(int)));
+    switch (o.vcycle_prec) {
+    case AMG_FP64: build_deep<double, double>(h); break;
+    case AMG_FP32: build_deep<float, float>(h); break;
+    default: build_deep<float, __nv_bfloat16>(h); break;
+    }
     h->w.alloc(n); h->r.alloc(n); h->xb.alloc(n); h->bb.alloc(n);
     h->hist.alloc((size_t)o.maxit + 2);
     h->partials.alloc((size_t)reduce_grid() * KMAX1);
@@ -425,7 +450,17 @@ struct VCycle {
         const double bytes = (sizeof(V) + 4.0) * (double)(F.v64.n + B.v64.n) + 12.0 * 2.0 * n +
                              sizeof(T) * (1.0 + (B.d64.n || F.d64.n ? 1.0 : 0.0) + 3.0) * n;
         tmark_begin(h, 2);
-        if (h->opt.persistent) {
+        // persistent 2: dataflow solve (no level barriers) on every level;
+        // persistent 1: one cooperative launch with level barriers where there
+        // are many schedule levels (natural order), colour classes as
+        // separate launches; persistent 0: one launch per schedule level
+        if (h->opt.persistent == 2) {
+            if (Lv.wy_sent != (int)sizeof(T)) {
+                fill_sentinel<T>(y, (size_t)Lv.A.n, s);
+                Lv.wy_sent = (int)sizeof(T);
+            }
+            sweep_pair_df<T, V>(view(F), fd, view(B), bd, in, y, t, h->bar.get(), h->err.get(), s);
+        } else if (h->opt.persistent && F.nlev + B.nlev > PERSISTENT_MIN_LEVELS) {
             sweep_pair_coop<T, V>(view(F), fd, view(B), bd, in, y, t, h->bar.get(), h->err.get(), s);
         } else {
             sweep<T, V>(view(F), in, y, fd, s);
@@ -452,6 +487,12 @@ struct VCycle {
     // g = C_l(h): the inexact solve of level l >= 1
     void level_solve(int l, const T *hrhs, T *g) {
         Level &Lv = L(l);
+        if (l >= h->deep_first) {
+            const DeepLevel<T, V> *d = reinterpret_cast<const DeepLevel<T, V> *>(h->deep_desc.get()) +
+                                       (l - h->deep_first);
+            deep_vcycle<T, V>(d, nlev() - l, s);
+            return;
+        }
         if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 0, 0, s); return; }
         const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
         T *res = ws(Lv.wres);
@@ -527,6 +568,49 @@ template <> SweepView<float, __nv_bfloat16> VCycle<float, __nv_bfloat16>::view(S
                                            S.ci.get(), S.v16.get(), S.d32.n ? S.d32.get() : nullptr};
 }
 
+// Device descriptors of the levels run by the single-block V-cycle.
+template <typename T, typename V>
+static void build_deep(amg_handle *h) {
+    const int nl = (int)h->lev.size();
+    const auto &o = h->opt;
+    h->deep_first = 1 << 30;
+    if (!o.deep_block_max || o.deep_inner != 1) return;
+    int first = nl;
+    for (int l = nl - 1; l >= 2; --l) {
+        if (h->lev[l]->A.n > o.deep_block_max) break;
+        first = l;
+    }
+    if (first >= nl) return;
+    VCycle<T, V> vc{h, h->stream};
+    std::vector<DeepLevel<T, V>> d(nl - first);
+    for (int l = first; l < nl; ++l) {
+        Level &Lv = *h->lev[l];
+        DeepLevel<T, V> &D = d[l - first];
+        memset(&D, 0, sizeof(D));
+        D.n = Lv.A.n;
+        D.dense = Lv.dense ? 1 : 0;
+        D.has_child = vc.has_child(l) ? 1 : 0;
+        D.rp = Lv.A.rp.get();
+        D.ci = Lv.A.ci.get();
+        D.v = vc.vals(Lv, false);
+        if (!Lv.dense) { D.fwd = vc.view(Lv.fwd); D.bwd = vc.view(Lv.bwd); }
+        D.inv = Lv.inv.get();
+        D.agg = Lv.agg.get();
+        D.mptr = Lv.mptr.get();
+        D.midx = Lv.midx.get();
+        D.h = VCycle<T, V>::ws(Lv.wh);
+        D.g = VCycle<T, V>::ws(Lv.wg);
+        D.t = VCycle<T, V>::ws(Lv.wt);
+        D.y = VCycle<T, V>::ws(Lv.wy);
+        D.r = VCycle<T, V>::ws(Lv.wr);
+    }
+    h->deep_desc.alloc(sizeof(DeepLevel<T, V>) * d.size());
+    CU(cudaMemcpyAsync(h->deep_desc.get(), d.data(), sizeof(DeepLevel<T, V>) * d.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->deep_first = first;
+}
+
 // q = B~^{-1} zin (or B~^{-T} zin) at level 0 in the V-cycle type.
 template <typename T, typename V>
 static void precond0(amg_handle *h, const T *zin, T *zout, bool transpose) {
@@ -560,31 +644,43 @@ static void enqueue_iteration(amg_handle *h, bool transpose) {
     apply_precond_vtype(h, transpose);
     // algorithmic bytes of w = A z: values + columns, row pointers, z once, w once
     const double bytes = 12.0 * M.nnz + 4.0 * (M.n + 1) + (f64 ? 8.0 : 4.0) * M.n + 8.0 * M.n;
+    const Sell &SL = transpose ? L0.sellT : L0.sell;
     tmark_begin(h, 1);
-    if (f64) spmv_f64(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), h->zout64.get(), h->w.get(), s);
-    else spmv_f64_xf32(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), h->zout32.get(), h->w.get(), s);
+    if (f64) sell_spmv<double>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(), h->zout64.get(), nullptr,
+                               h->w.get(), 0, s);
+    else sell_spmv<float>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(), h->zout32.get(), nullptr,
+                          h->w.get(), 0, s);
     tmark_end(h, 1, bytes);
+    (void)M;
     if (f64) store_zj<double>(n, dst, h->zout64.get(), h->Zd.get(), s);
     else store_zj<float>(n, dst, h->zout32.get(), h->Zf.get(), s);
-    mdot(n, dst, h->w.get(), h->V.get(), n, h->partials.get(), h->ticket.get(), dst->h1, s);
-    // a CGS2 pass reads the K = j+1 basis vectors and w and writes w; K is
-    // known only on the device, so the bytes use the cycle's mean K = (m+1)/2
-    tmark_begin(h, 3);
-    cgs_update(n, dst, dst->h1, h->w.get(), h->V.get(), n, 1, h->partials.get(), h->ticket.get(), dst->h2, s);
-    tmark_end(h, 3, 8.0 * (double)n * (0.5 * (h->opt.restart + 1) + 2.0));
-    cgs_update(n, dst, dst->h2, h->w.get(), h->V.get(), n, 0, h->partials.get(), h->ticket.get(), dst->nrm2, s);
+    // K = j+1 basis vectors are known only on the device, so the bytes use
+    // the cycle's mean K = (m+1)/2
+    const double K = 0.5 * (h->opt.restart + 1);
+    if (h->opt.orthog == AMG_ORTHO_MGS) {
+        // step k reads w, v_k, v_{k+1} and writes w; the first dot reads w, v_0
+        tmark_begin(h, 3);
+        mgs(n, dst, h->w.get(), h->V.get(), n, h->partials.get(), h->bar.get(), h->err.get(), s);
+        tmark_end(h, 3, 8.0 * (double)n * (4.0 * K + 2.0));
+    } else {
+        mdot(n, dst, h->w.get(), h->V.get(), n, h->partials.get(), h->ticket.get(), dst->h1, s);
+        // a CGS2 pass reads the K basis vectors and w and writes w
+        tmark_begin(h, 3);
+        cgs_update(n, dst, dst->h1, h->w.get(), h->V.get(), n, 1, h->partials.get(), h->ticket.get(), dst->h2, s);
+        tmark_end(h, 3, 8.0 * (double)n * (K + 2.0));
+        cgs_update(n, dst, dst->h2, h->w.get(), h->V.get(), n, 0, h->partials.get(), h->ticket.get(), dst->nrm2, s);
+    }
     givens(dst, s);
     scale_next(n, h->w.get(), h->V.get(), dst, s);
     CU(cudaMemcpyAsync(h->hflags, &dst->stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
 }
 
-// Runs one inner iteration, replaying a captured CUDA graph when enabled.
-static void run_iteration(amg_handle *h, bool transpose) {
+// Queues one inner iteration, replaying a captured CUDA graph when enabled
+// (captured on first use, once per handle and direction).  No synchronisation.
+static void launch_iteration(amg_handle *h, bool transpose) {
     const int d = transpose ? 1 : 0;
     if (!h->opt.use_graphs) {
         enqueue_iteration(h, transpose);
-        CU(cudaStreamSynchronize(h->stream));
-        tcollect(h);
         return;
     }
     if (!h->gexec[d]) {
@@ -616,14 +712,19 @@ static void run_iteration(amg_handle *h, bool transpose) {
     CU(cudaGraphLaunch(h->gexec[d], h->stream));
     count_launch(h->gnodes[d]);
     h->t_bytes += h->gbytes[d];
+}
+
+// Waits for the queued iteration and folds its kernel timings.
+static void collect_iteration(amg_handle *h, bool transpose) {
     CU(cudaStreamSynchronize(h->stream));
-    tcollect(h, h->gpairs[d]);
+    if (h->opt.use_graphs) tcollect(h, h->gpairs[transpose ? 1 : 0]);
+    else tcollect(h);
 }
 
 static void outer_residual(amg_handle *h, const double *b, const double *x, double *r, bool transpose) {
     Level &L0 = *h->lev[0];
-    const DCsr &M = transpose ? L0.AT : L0.A;
-    residual_f64(M.n, M.nnz, M.rp.get(), M.ci.get(), M.v.get(), x, b, r, h->stream);
+    const Sell &SL = transpose ? L0.sellT : L0.sell;
+    sell_spmv<double>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(), x, b, r, 1, h->stream);
 }
 
 static double read_norm(amg_handle *h, const double *v) {
@@ -635,77 +736,118 @@ static double read_norm(amg_handle *h, const double *v) {
     return std::sqrt(r);
 }
 
-static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, amg_stats_t *stats, bool transpose) {
-    const auto t0 = std::chrono::steady_clock::now();
+// One FGMRES(m) solve as a host-side state machine, so that the batched
+// driver can advance many systems (each on its own stream) together:
+// begin() computes ||b|| and the initial residual and starts a cycle;
+// launch()/collect() run one inner iteration; at the end of a cycle the
+// solution is updated, the true residual decides convergence, and a new
+// cycle starts.  Kernels and their order are those of a single solve.
+struct Run {
+    amg_handle *h = nullptr;
+    const double *b_in = nullptr, *b = nullptr;
+    double *x_io = nullptr;
+    bool x_dev = false, transpose = false, done = false;
+    double tol = 0.0, bnorm = 0.0, relres = 0.0;
+    int status = AMG_OK, total = 0, restarts = 0, j = 0;
+    int64_t launches0 = 0;
+    std::chrono::steady_clock::time_point t0;
+    DBuf<double> tb;
+};
+
+static void start_cycle(Run &R) {
+    amg_handle *h = R.h;
+    if (R.relres <= R.tol) { R.done = true; return; }
+    if (R.total >= h->opt.maxit) { R.status = AMG_ERR_NOT_CONVERGED; R.done = true; return; }
+    // the state's nrm2 holds ||r||^2 from read_norm
+    restart_scale(h->n, h->r.get(), h->V.get(), h->st.get(), h->stream);
+    R.j = 0;
+}
+
+static void run_begin(Run &R) {
+    amg_handle *h = R.h;
+    R.t0 = std::chrono::steady_clock::now();
+    R.launches0 = launch_count();
     enter(h);
-    const int64_t launches0 = launch_count();
     cudaStream_t s = h->stream;
     const size_t n = h->n;
-    const int m = h->opt.restart;
-    const bool x_dev = is_device_ptr(x_io);
+    R.x_dev = is_device_ptr(R.x_io);
+    R.b = to_device(R.b_in, n, R.tb, s);
     double *x = h->xb.get();
-    const double *b;
-    DBuf<double> tb;
-    b = to_device(b_in, n, tb, s);
-    if (is_device_ptr(b_in)) b = b_in;
-    if (x_dev) CU(cudaMemcpyAsync(x, x_io, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    else CU(cudaMemcpyAsync(x, x_io, n * sizeof(double), cudaMemcpyHostToDevice, s));
-
-    FgState *dst = h->st.get();
+    if (R.x_dev) CU(cudaMemcpyAsync(x, R.x_io, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else CU(cudaMemcpyAsync(x, R.x_io, n * sizeof(double), cudaMemcpyHostToDevice, s));
     FgState &hs = *h->hst;
     memset(&hs, 0, sizeof(FgState));
-    hs.m = m; hs.maxit = h->opt.maxit; hs.hist_cap = h->opt.maxit + 2; hs.tol = tol;
+    hs.m = h->opt.restart; hs.maxit = h->opt.maxit; hs.hist_cap = h->opt.maxit + 2; hs.tol = R.tol;
     hs.hist = h->hist.get();
-    int status = AMG_OK, total = 0, restarts = 0;
-    double relres = 0.0;
-    const double bnorm = read_norm(h, b);
     h->last_hist.clear();
-    if (!std::isfinite(bnorm)) status = AMG_ERR_NUMERIC;
-    else if (bnorm == 0.0) {
+    R.bnorm = read_norm(h, R.b);
+    if (!std::isfinite(R.bnorm)) { R.status = AMG_ERR_NUMERIC; R.done = true; return; }
+    if (R.bnorm == 0.0) {
         CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
         h->last_hist.push_back(0.0);
-    } else {
-        hs.bnorm = bnorm;
-        hs.hist_len = 1;
-        CU(cudaMemcpyAsync(dst, &hs, sizeof(FgState), cudaMemcpyHostToDevice, s));
-        outer_residual(h, b, x, h->r.get(), transpose);
-        double beta = read_norm(h, h->r.get());      // leaves ||r0||^2 in the state for the restart
-        relres = beta / bnorm;
-        CU(cudaMemcpyAsync(h->hist.get(), &relres, sizeof(double), cudaMemcpyHostToDevice, s));
-        CU(cudaStreamSynchronize(s));
-        if (!std::isfinite(relres)) status = AMG_ERR_NUMERIC;
-        while (status == AMG_OK) {
-            if (relres <= tol) break;
-            if (total >= h->opt.maxit) { status = AMG_ERR_NOT_CONVERGED; break; }
-            // the state's nrm2 holds ||r||^2 from read_norm
-            restart_scale(n, h->r.get(), h->V.get(), dst, s);
-            for (int j = 0; j < m; ++j) {
-                run_iteration(h, transpose);
-                if (h->hflags[0]) break;
-            }
-            CU(cudaMemcpyAsync(&hs, dst, sizeof(FgState), cudaMemcpyDeviceToHost, s));
-            CU(cudaStreamSynchronize(s));
-            total = hs.total;
-            if (hs.status) { status = hs.status; break; }
-            backsolve(dst, s);
-            if (h->opt.vcycle_prec == AMG_FP64) update_x<double>(n, dst, h->Zd.get(), n, x, s);
-            else update_x<float>(n, dst, h->Zf.get(), n, x, s);
-            outer_residual(h, b, x, h->r.get(), transpose);
-            const double beta = read_norm(h, h->r.get());
-            relres = beta / bnorm;
-            if (!std::isfinite(relres)) { status = AMG_ERR_NUMERIC; break; }
-            if (relres <= tol) break;
-            if (total >= h->opt.maxit) { status = AMG_ERR_NOT_CONVERGED; break; }
-            ++restarts;
-        }
-        CU(cudaMemcpyAsync(&hs, dst, sizeof(FgState), cudaMemcpyDeviceToHost, s));
+        R.done = true;
+        return;
+    }
+    hs.bnorm = R.bnorm;
+    hs.hist_len = 1;
+    CU(cudaMemcpyAsync(h->st.get(), &hs, sizeof(FgState), cudaMemcpyHostToDevice, s));
+    outer_residual(h, R.b, x, h->r.get(), R.transpose);
+    const double beta = read_norm(h, h->r.get());      // leaves ||r0||^2 in the state for the restart
+    R.relres = beta / R.bnorm;
+    CU(cudaMemcpyAsync(h->hist.get(), &R.relres, sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    if (!std::isfinite(R.relres)) { R.status = AMG_ERR_NUMERIC; R.done = true; return; }
+    start_cycle(R);
+}
+
+static void end_cycle(Run &R) {
+    amg_handle *h = R.h;
+    cudaStream_t s = h->stream;
+    FgState &hs = *h->hst;
+    FgState *dst = h->st.get();
+    CU(cudaMemcpyAsync(&hs, dst, sizeof(FgState), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    R.total = hs.total;
+    if (hs.status) { R.status = hs.status; R.done = true; return; }
+    const size_t n = h->n;
+    double *x = h->xb.get();
+    backsolve(dst, s);
+    if (h->opt.vcycle_prec == AMG_FP64) update_x<double>(n, dst, h->Zd.get(), n, x, s);
+    else update_x<float>(n, dst, h->Zf.get(), n, x, s);
+    outer_residual(h, R.b, x, h->r.get(), R.transpose);
+    const double beta = read_norm(h, h->r.get());
+    R.relres = beta / R.bnorm;
+    if (!std::isfinite(R.relres)) { R.status = AMG_ERR_NUMERIC; R.done = true; return; }
+    if (R.relres <= R.tol) { R.done = true; return; }
+    if (R.total >= h->opt.maxit) { R.status = AMG_ERR_NOT_CONVERGED; R.done = true; return; }
+    ++R.restarts;
+    start_cycle(R);
+}
+
+static void run_launch(Run &R) { launch_iteration(R.h, R.transpose); }
+
+static void run_collect(Run &R) {
+    collect_iteration(R.h, R.transpose);
+    ++R.j;
+    if (R.h->hflags[0] || R.j >= R.h->opt.restart) end_cycle(R);
+}
+
+static int run_end(Run &R, amg_stats_t *stats) {
+    amg_handle *h = R.h;
+    cudaStream_t s = h->stream;
+    const size_t n = h->n;
+    FgState &hs = *h->hst;
+    if (h->last_hist.empty() && R.bnorm != 0.0 && std::isfinite(R.bnorm)) {
+        CU(cudaMemcpyAsync(&hs, h->st.get(), sizeof(FgState), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         h->last_hist.resize(hs.hist_len);
         if (hs.hist_len)
-            CU(cudaMemcpyAsync(h->last_hist.data(), h->hist.get(), sizeof(double) * hs.hist_len, cudaMemcpyDeviceToHost, s));
+            CU(cudaMemcpyAsync(h->last_hist.data(), h->hist.get(), sizeof(double) * hs.hist_len,
+                               cudaMemcpyDeviceToHost, s));
     }
-    if (x_dev) CU(cudaMemcpyAsync(x_io, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    else CU(cudaMemcpyAsync(x_io, x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    double *x = h->xb.get();
+    if (R.x_dev) CU(cudaMemcpyAsync(R.x_io, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else CU(cudaMemcpyAsync(R.x_io, x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     int derr = 0;
     CU(cudaMemcpyAsync(&derr, h->err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -713,24 +855,36 @@ static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, a
         CU(cudaMemsetAsync(h->err.get(), 0, sizeof(int), s));
         CU(cudaMemsetAsync(h->bar.get(), 0, 2 * sizeof(unsigned int), s));
         CU(cudaStreamSynchronize(s));
-        t_last_error = "a grid-barrier wait gave up (results invalid)";
-        status = AMG_ERR_LIMIT;
+        for (auto &L : h->lev) L->wy_sent = 0;
+        t_last_error = "a grid-barrier or dataflow wait gave up (results invalid)";
+        R.status = AMG_ERR_LIMIT;
     }
     const auto t1 = std::chrono::steady_clock::now();
     if (stats) {
-        stats->status = status;
-        stats->iters = total;
-        stats->restarts = restarts;
+        stats->status = R.status;
+        stats->iters = R.total;
+        stats->restarts = R.restarts;
         stats->nlevels = (int)h->lev.size();
-        stats->rel_res_true = relres;
+        stats->rel_res_true = R.relres;
         stats->setup_ms = h->setup_ms;
-        stats->solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        stats->solve_ms = std::chrono::duration<double, std::milli>(t1 - R.t0).count();
         stats->n_coarse = h->lev.size() > 1 ? h->lev[1]->A.n : 0;
         stats->nnz_coarse = h->lev.size() > 1 ? h->lev[1]->A.nnz : 0;
         stats->n_colors = h->lev[0]->fwd.nlev;
-        stats->kernel_launches = launch_count() - launches0;
+        stats->kernel_launches = launch_count() - R.launches0;
     }
-    return status;
+    return R.status;
+}
+
+static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, amg_stats_t *stats, bool transpose) {
+    Run R;
+    R.h = h; R.b_in = b_in; R.x_io = x_io; R.tol = tol; R.transpose = transpose;
+    run_begin(R);
+    while (!R.done) {
+        run_launch(R);
+        run_collect(R);
+    }
+    return run_end(R, stats);
 }
 
 }  // namespace amg
@@ -799,6 +953,8 @@ int amg_default_options(amg_options_t *o) {
     o->build_adjoint = 0;
     o->use_graphs = 1;
     o->persistent = 1;
+    o->deep_block_max = 0;
+    o->orthog = AMG_ORTHO_MGS;
     o->seed = 0;
     return AMG_OK;
 }
@@ -807,7 +963,8 @@ static void check_options(const amg_options_t &o) {
     if (o.passes < 1 || o.passes > 8 || o.coarse_inner < 1 || o.deep_inner < 1 || o.dense_max < 0 ||
         o.dense_max > 4096 || o.max_levels < 2 || o.max_levels > 24 || o.restart < 1 || o.restart > KMAX1 - 1 ||
         o.maxit < 0 || o.vcycle_prec < 0 || o.vcycle_prec > 2 || o.order_fine < 0 || o.order_fine > 1 ||
-        o.order_coarse < 0 || o.order_coarse > 1 || o.coloring < 0 || o.coloring > 1)
+        o.order_coarse < 0 || o.order_coarse > 1 || o.coloring < 0 || o.coloring > 1 || o.deep_block_max < 0 ||
+        o.persistent < 0 || o.persistent > 2 || o.orthog < 0 || o.orthog > 1)
         fail(AMG_ERR_INVALID_ARG, "option out of range (restart <= 31, dense_max <= 4096, 2 <= max_levels <= 24)");
 }
 
@@ -833,6 +990,8 @@ int amg_setup(const amg_csr_t *A, const amg_options_t *opt, void *stream, amg_ha
 
 void amg_destroy(amg_handle_t *h) {
     if (!h) return;
+    for (amg_handle *sub : h->subs) amg_destroy(sub);
+    h->subs.clear();
     try {
         cudaStreamSynchronize(h->stream);
         if (h->hst) cudaFreeHost(h->hst);
@@ -851,6 +1010,7 @@ void amg_destroy(amg_handle_t *h) {
 int amg_solve(amg_handle_t *h, const double *b, double *x, double tol, amg_stats_t *stats) {
     ABI_TRY
     if (!h || !b || !x) fail(AMG_ERR_INVALID_ARG, "amg_solve: null argument");
+    if (!h->subs.empty()) fail(AMG_ERR_INVALID_ARG, "amg_solve: batched handle (use amg_solve_batched)");
     if (!(tol >= 0.0)) fail(AMG_ERR_INVALID_ARG, "amg_solve: tol must be >= 0");
     return fgmres(h, b, x, tol, stats, false);
     ABI_CATCH
@@ -859,10 +1019,116 @@ int amg_solve(amg_handle_t *h, const double *b, double *x, double tol, amg_stats
 int amg_adjoint(amg_handle_t *h, const double *g, double *lambda, double tol, amg_stats_t *stats) {
     ABI_TRY
     if (!h || !g || !lambda) fail(AMG_ERR_INVALID_ARG, "amg_adjoint: null argument");
+    if (!h->subs.empty()) fail(AMG_ERR_INVALID_ARG, "amg_adjoint: batched handle");
     if (!h->adjoint_ready) fail(AMG_ERR_INVALID_ARG, "amg_adjoint: setup without build_adjoint");
     if (!(tol >= 0.0)) fail(AMG_ERR_INVALID_ARG, "amg_adjoint: tol must be >= 0");
     return fgmres(h, g, lambda, tol, stats, true);
     ABI_CATCH
+}
+
+int amg_setup_batched(const amg_csr_t *systems, int32_t count, const amg_options_t *opt, void *stream,
+                      amg_handle_t **out) {
+    if (out) *out = nullptr;
+    ABI_TRY
+    if (!systems || count <= 0 || !out) fail(AMG_ERR_INVALID_ARG, "amg_setup_batched: bad argument");
+    auto t0 = std::chrono::steady_clock::now();
+    std::unique_ptr<amg_handle> B(new amg_handle());
+    if (opt) B->opt = *opt;
+    else amg_default_options(&B->opt);
+    check_options(B->opt);
+    B->ustream = (cudaStream_t)stream;
+    B->subs.assign(count, nullptr);
+    // independent systems: set up concurrently from a few host threads, each
+    // system on its own internal stream
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    std::vector<int> st(count, AMG_OK);
+    std::vector<std::string> msg(count);
+    std::atomic<int> next{0};
+    std::atomic<int64_t> launches{0};
+    const int nth = std::max(1, std::min<int>(count, 8));
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        const int64_t l0 = launch_count();
+        for (;;) {
+            const int k = next.fetch_add(1);
+            if (k >= count) break;
+            amg_handle_t *sub = nullptr;
+            st[k] = amg_setup(&systems[k], &B->opt, stream, &sub);
+            if (st[k] != AMG_OK) msg[k] = amg_last_error();
+            B->subs[k] = sub;
+        }
+        launches += launch_count() - l0;
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t) th.emplace_back(work);
+    for (auto &t : th) t.join();
+    count_launch(launches.load());
+    for (int k = 0; k < count; ++k)
+        if (st[k] != AMG_OK) {
+            const int code = st[k];
+            const std::string m = "system " + std::to_string(k) + ": " + msg[k];
+            for (amg_handle *sub : B->subs) amg_destroy(sub);
+            B->subs.clear();
+            fail(code, m);
+        }
+    B->offs.assign(count + 1, 0);
+    for (int k = 0; k < count; ++k) B->offs[k + 1] = B->offs[k] + systems[k].n;
+    B->n = (int)std::min<int64_t>(B->offs[count], 0x7fffffff);
+    B->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = B.release();
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_solve_batched(amg_handle_t *h, const double *b_cat, double *x_cat, double tol, amg_stats_t *per_system) {
+    ABI_TRY
+    if (!h || h->subs.empty() || !b_cat || !x_cat) fail(AMG_ERR_INVALID_ARG, "amg_solve_batched: bad argument");
+    if (!(tol >= 0.0)) fail(AMG_ERR_INVALID_ARG, "amg_solve_batched: tol must be >= 0");
+    const int count = (int)h->subs.size();
+    std::vector<Run> R(count);
+    for (int k = 0; k < count; ++k) {
+        R[k].h = h->subs[k];
+        R[k].b_in = b_cat + h->offs[k];
+        R[k].x_io = x_cat + h->offs[k];
+        R[k].tol = tol;
+        CU(cudaStreamSynchronize(h->ustream));
+        R[k].h->ustream = h->ustream;
+        run_begin(R[k]);
+    }
+    // one loop over the batch: every active system queues its inner
+    // iteration on its own stream, then each is collected; converged systems
+    // drop out (mask), the others continue
+    for (;;) {
+        bool any = false;
+        for (int k = 0; k < count; ++k)
+            if (!R[k].done) { run_launch(R[k]); any = true; }
+        if (!any) break;
+        for (int k = 0; k < count; ++k)
+            if (!R[k].done) run_collect(R[k]);
+    }
+    int status = AMG_OK;
+    for (int k = 0; k < count; ++k) {
+        const int sk = run_end(R[k], per_system ? per_system + k : nullptr);
+        if (sk != AMG_OK && (status == AMG_OK || status == AMG_ERR_NOT_CONVERGED)) status = sk;
+    }
+    return status;
+    ABI_CATCH
+}
+
+int amg_batch_size(amg_handle_t *h, int32_t *count, int64_t *offsets) {
+    ABI_TRY
+    if (!h || !count) fail(AMG_ERR_INVALID_ARG, "amg_batch_size: null argument");
+    *count = (int32_t)h->subs.size();
+    if (offsets)
+        for (size_t k = 0; k < h->offs.size(); ++k) offsets[k] = h->offs[k];
+    return AMG_OK;
+    ABI_CATCH
+}
+
+amg_handle_t *amg_batch_member(amg_handle_t *h, int32_t k) {
+    if (!h || k < 0 || k >= (int)h->subs.size()) return nullptr;
+    return h->subs[k];
 }
 
 int amg_get_history(amg_handle_t *h, double *out, int32_t cap, int32_t *len) {

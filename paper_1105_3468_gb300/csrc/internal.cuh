@@ -74,6 +74,19 @@ struct DCsr {
     DBuf<double> v;     // [nnz]
 };
 
+// SELL-32 copy of a CSR matrix: slices of 32 consecutive rows, each slice
+// padded to its longest row and stored column-major (entry k of row r of
+// slice s at ptr[s] + 32 k + r), so a warp's load of entry k is contiguous.
+// Padding repeats the row's diagonal column with value 0.
+struct Sell {
+    int n = 0, nslices = 0;
+    int64_t padded = 0;
+    DBuf<int64_t> ptr;      // [nslices + 1]
+    DBuf<int> ci;           // [padded]
+    DBuf<double> v;         // [padded]
+};
+void build_sell(const DCsr &A, const double *vals, Sell &S, cudaStream_t s);
+
 // Row-scheduled triangular factor for one sweep direction.
 struct Sweep {
     int nlev = 0;                   // schedule levels

@@ -40,13 +40,12 @@ void *dmalloc(size_t bytes) {
 void dfree(void *p) { cudaFree(p); }
 
 int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {               // initialised once, thread-safe
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return sms;
 }
 
@@ -272,14 +271,8 @@ __global__ void k_keys_from_int(const int *a, uint32_t *k, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) k[i] = (uint32_t)a[i];
 }
 __global__ void k_count_keys(const uint32_t *k, int n, int *cnt) {
-    // k sorted: count[k] = run length; each run start writes its length
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (i == 0 || k[i] != k[i - 1]) {
-            int j = i + 1;
-            while (j < n && k[j] == k[i]) ++j;
-            cnt[k[i]] = j - i;
-        }
-    }
+    // integer histogram: the counts do not depend on the order of the atomics
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) atomicAdd(cnt + k[i], 1);
 }
 __global__ void k_gather_int(const int *src, const int *idx, int *dst, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];

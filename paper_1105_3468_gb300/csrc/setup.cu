@@ -528,41 +528,76 @@ void elimination_positions(int n, const int *label, int nlabels, int *pos, cudaS
 }
 
 // ------------------------------------------------------------------ sweep schedules
-// Longest-path depth in the dependency graph of the forward (pos[j] <
-// pos[i]) or backward (pos[j] > pos[i]) solve, by monotone relaxation.
-__global__ void k_level_relax(int n, const int *rp, const int *ci, const int *pos, int *lev, int fwd,
-                              int *changed) {
-    int ch = 0;
+// Longest-path depth of each row in the dependency graph of the forward
+// (pos[j] < pos[i]) or backward (pos[j] > pos[i]) solve, by frontier rounds
+// (Kahn's algorithm): a row enters round r when the last of its
+// dependencies was in round r-1, so its round is 1 + the largest depth of
+// its dependencies.  Work O(nnz) over all rounds.
+__global__ void k_dep_count(int n, const int *rp, const int *ci, const int *pos, int fwd, int *indeg) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int pi = pos[i], m = -1;
+        const int pi = pos[i];
+        int m = 0;
         for (int e = rp[i]; e < rp[i + 1]; ++e) {
-            int j = ci[e];
-            int pj = pos[j];
-            if (fwd ? (pj < pi) : (pj > pi)) m = max(m, ld_volatile(lev + j));
+            const int pj = pos[ci[e]];
+            if (fwd ? (pj < pi) : (pj > pi)) ++m;
         }
-        int nl = m + 1;
-        if (nl > ld_volatile(lev + i)) { *(volatile int *)(lev + i) = nl; ch = 1; }
+        indeg[i] = m;
     }
-    if (ch) atomicExch(changed, 1);
+}
+
+__global__ void k_frontier_init(int n, const int *indeg, int *front, int *count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (indeg[i] == 0) front[atomicAdd(count, 1)] = i;
+}
+
+// rows of the frontier get depth r; their dependents (column j of the
+// pattern = rows i with a_ij stored) lose one dependency
+__global__ void k_frontier_step(const int *front, int cnt, int r, const int *trp, const int *tci, const int *pos,
+                                int fwd, int *indeg, int *lev, int *next, int *ncount) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const int j = front[t];
+        lev[j] = r;
+        const int pj = pos[j];
+        for (int e = trp[j]; e < trp[j + 1]; ++e) {
+            const int i = tci[e];
+            const int pi = pos[i];
+            if (!(fwd ? (pj < pi) : (pj > pi))) continue;
+            if (atomicSub(indeg + i, 1) == 1) next[atomicAdd(ncount, 1)] = i;
+        }
+    }
 }
 
 static int schedule_levels(const DCsr &A, const int *pos, int fwd, int *lev, cudaStream_t s) {
-    DBuf<int> changed(1);
-    fill_int(lev, 0, A.n, s);
+    const int n = A.n;
+    DBuf<int> trp, tci, tsrc, indeg(n), fa(n), fb(n), cnt(2);
+    csr_transpose(n, A.nnz, A.rp.get(), A.ci.get(), trp, tci, tsrc, s);
+    k_dep_count<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), pos, fwd, indeg.get());
+    CU_LAUNCH("k_dep_count"); count_launch();
+    CU(cudaMemsetAsync(cnt.get(), 0, 2 * sizeof(int), s));
+    k_frontier_init<<<grid_for(n, 256), 256, 0, s>>>(n, indeg.get(), fa.get(), cnt.get());
+    CU_LAUNCH("k_frontier_init"); count_launch();
     int *h = nullptr;
     CU(cudaMallocHost(&h, sizeof(int)));
-    int it = 0;
-    for (;; ++it) {
-        if (it > A.n + 2) { cudaFreeHost(h); fail(8, "sweep schedule did not settle"); }
-        CU(cudaMemsetAsync(changed.get(), 0, sizeof(int), s));
-        k_level_relax<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp.get(), A.ci.get(), pos, lev, fwd, changed.get());
-        CU_LAUNCH("k_level_relax"); count_launch();
-        CU(cudaMemcpyAsync(h, changed.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(h, cnt.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    int c = *h, r = 0, done = 0;
+    int *cur = fa.get(), *nxt = fb.get();
+    while (c > 0) {
+        if (r > n) { cudaFreeHost(h); fail(8, "sweep schedule did not settle"); }
+        CU(cudaMemsetAsync(cnt.get() + 1, 0, sizeof(int), s));
+        k_frontier_step<<<grid_for(c, 256), 256, 0, s>>>(cur, c, r, trp.get(), tci.get(), pos, fwd, indeg.get(), lev,
+                                                         nxt, cnt.get() + 1);
+        CU_LAUNCH("k_frontier_step"); count_launch();
+        CU(cudaMemcpyAsync(h, cnt.get() + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        if (!*h) break;
+        done += c;
+        c = *h;
+        std::swap(cur, nxt);
+        ++r;
     }
     cudaFreeHost(h);
-    return max_of(lev, A.n, s) + 1;
+    if (done != n) fail(8, "sweep schedule: dependency cycle");
+    return r;
 }
 
 __global__ void k_sweep_count(int n, const int *rows, const int *rp, const int *ci, const int *pos, int fwd,
@@ -628,12 +663,14 @@ static void build_sweep(const DCsr &A, const int *pos, const double *lu, int fwd
 // (k, j) with pos(j) > pos(k) whose (i, j) is stored.  Rows of one schedule
 // level only read rows of earlier levels, so a level runs in parallel.
 constexpr int ILU_CAP = 256;
+constexpr int ILU_WCAP = 256, ILU_WARPS = 4;   // rows up to ILU_WCAP entries: warp kernel
 
 __global__ void k_ilu_rows(const int *rows, int count, const int *rp, const int *ci, const int *pos,
                            const int *dpos, double *lu, int *breakdown, int *overflow) {
     int lp[ILU_CAP], le[ILU_CAP];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
         const int i = rows[t], pi = pos[i], rb = rp[i], re = rp[i + 1];
+        if (re - rb <= ILU_WCAP) continue;           // handled by the warp kernel
         int nl = 0;
         bool over = false;
         for (int e = rb; e < re; ++e) {
@@ -661,6 +698,78 @@ __global__ void k_ilu_rows(const int *rows, int count, const int *rp, const int 
         }
         double piv = lu[dpos[i]];
         if (piv == 0.0 || !isfinite(piv)) atomicExch(breakdown, 1);
+    }
+}
+
+// Warp-per-row variant for rows of at most ILU_WCAP entries: row i is staged
+// in shared memory, its L entries are ranked by pos in parallel, then for each
+// L entry k (in increasing pos) lane 0 divides and the lanes apply row k's U
+// part to the staged row (distinct columns per lane, so no two lanes update
+// the same entry).  Same operations in the same order per entry as the
+// thread-per-row kernel, hence bit-identical factors.
+
+__global__ void __launch_bounds__(32 * ILU_WARPS) k_ilu_rows_warp(const int *rows, int count, const int *rp,
+                                                                  const int *ci, const int *pos, const int *dpos,
+                                                                  double *lu, int *breakdown) {
+    __shared__ int s_col[ILU_WARPS][ILU_WCAP];
+    __shared__ int s_pos[ILU_WARPS][ILU_WCAP];
+    __shared__ double s_val[ILU_WARPS][ILU_WCAP];
+    __shared__ int s_ord[ILU_WARPS][ILU_WCAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = blockIdx.x * ILU_WARPS + w, nw = gridDim.x * ILU_WARPS;
+    for (int t = gw; t < count; t += nw) {
+        const int i = rows[t], rb = rp[i], len = rp[i + 1] - rb, pi = pos[i];
+        if (len > ILU_WCAP) continue;                // long rows: thread kernel
+        for (int q = lane; q < len; q += 32) {
+            const int c = ci[rb + q];
+            s_col[w][q] = c;
+            s_pos[w][q] = pos[c];
+            s_val[w][q] = lu[rb + q];
+        }
+        __syncwarp();
+        int nl = 0;
+        for (int q = lane; q < len; q += 32) {       // rank of each L entry by pos
+            const int pq = s_pos[w][q];
+            if (pq < pi) {
+                int r = 0;
+                for (int u = 0; u < len; ++u) r += (s_pos[w][u] < pq) ? 1 : 0;
+                s_ord[w][r] = q;
+            }
+        }
+        for (int q = 0; q < len; ++q) nl += (s_pos[w][q] < pi) ? 1 : 0;
+        __syncwarp();
+        for (int a = 0; a < nl; ++a) {
+            const int qk = s_ord[w][a];
+            const int k = s_col[w][qk], pk = s_pos[w][qk];
+            double lik = 0.0;
+            if (lane == 0) {
+                lik = __ddiv_rn(s_val[w][qk], lu[dpos[k]]);
+                s_val[w][qk] = lik;
+            }
+            lik = __shfl_sync(0xffffffffu, lik, 0);
+            __syncwarp();
+            for (int ekj = rp[k] + lane; ekj < rp[k + 1]; ekj += 32) {
+                const int j = ci[ekj];
+                if (pos[j] <= pk) continue;
+                int lo = 0, hi = len - 1;                // columns of row i ascend
+                while (lo <= hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int cm = s_col[w][mid];
+                    if (cm == j) {
+                        s_val[w][mid] = __dsub_rn(s_val[w][mid], __dmul_rn(lik, lu[ekj]));
+                        break;
+                    }
+                    if (cm < j) lo = mid + 1; else hi = mid - 1;
+                }
+            }
+            __syncwarp();
+        }
+        for (int q = lane; q < len; q += 32) lu[rb + q] = s_val[w][q];
+        if (lane == 0) {
+            const double piv = s_val[w][dpos[i] - rb];
+            if (piv == 0.0 || !isfinite(piv)) atomicExch(breakdown, 1);
+        }
+        __syncwarp();
     }
 }
 
@@ -694,12 +803,23 @@ void ilu0_factor(const DCsr &A, const int *pos, DBuf<double> &lu, Sweep &fwd, Sw
         CU(cudaMemcpyAsync(tmp.lev_ptr.data(), lp.get(), sizeof(int) * (nf + 1), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
     }
+    bool long_rows = false;
+    {
+        std::vector<int> hrp(n + 1);
+        CU(cudaMemcpy(hrp.data(), A.rp.get(), sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n && !long_rows; ++i) long_rows = hrp[i + 1] - hrp[i] > ILU_WCAP;
+    }
     for (int l = 0; l < nf; ++l) {
         const int b = tmp.lev_ptr[l], cnt = tmp.lev_ptr[l + 1] - b;
         if (cnt <= 0) continue;
-        k_ilu_rows<<<grid_for(cnt, 128), 128, 0, s>>>(tmp.rows.get() + b, cnt, A.rp.get(), A.ci.get(), pos,
-                                                      dpos.get(), lu.get(), flags.get(), flags.get() + 1);
-        CU_LAUNCH("k_ilu_rows"); count_launch();
+        k_ilu_rows_warp<<<grid_for((size_t)cnt * 32, 32 * ILU_WARPS), 32 * ILU_WARPS, 0, s>>>(
+            tmp.rows.get() + b, cnt, A.rp.get(), A.ci.get(), pos, dpos.get(), lu.get(), flags.get());
+        CU_LAUNCH("k_ilu_rows_warp"); count_launch();
+        if (long_rows) {
+            k_ilu_rows<<<grid_for(cnt, 128), 128, 0, s>>>(tmp.rows.get() + b, cnt, A.rp.get(), A.ci.get(), pos,
+                                                          dpos.get(), lu.get(), flags.get(), flags.get() + 1);
+            CU_LAUNCH("k_ilu_rows"); count_launch();
+        }
     }
     int hf[2];
     CU(cudaMemcpyAsync(hf, flags.get(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -794,7 +914,7 @@ __global__ void k_gj_elim(int n, int k, double *M, const double *f) {
         const int i = (int)(t / (2 * n)), j = (int)(t % (2 * n));
         if (i == k) continue;
         const double fi = f[i];
-        if (fi != 0.0) M[t] = M[t] - fi * rk[j];
+        if (fi != 0.0) M[t] = __dsub_rn(M[t], __dmul_rn(fi, rk[j]));
     }
 }
 
@@ -824,6 +944,64 @@ void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
     k_extract_inverse<<<grid_for((size_t)n * n, 256), 256, 0, s>>>(n, M.get(), inv.get());
     CU_LAUNCH("k_extract_inverse"); count_launch();
     if (read_int(bd.get(), s)) fail(5, "dense solve of the last level: singular matrix");
+}
+
+// ------------------------------------------------------------------ SELL-32 layout
+__global__ void k_sell_width(int n, const int *rp, int nslices, int *w) {
+    for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += gridDim.x * blockDim.x) {
+        int m = 0;
+        for (int r = 0; r < 32; ++r) {
+            const int i = sl * 32 + r;
+            if (i < n) m = max(m, rp[i + 1] - rp[i]);
+        }
+        w[sl] = m;
+    }
+}
+
+__global__ void k_sell_fill(int n, const int *rp, const int *ci, const double *v, const int64_t *ptr, int *sci,
+                            double *sv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ((n + 31) / 32) * 32; i += gridDim.x * blockDim.x) {
+        const int sl = i >> 5, r = i & 31;
+        const int64_t base = ptr[sl];
+        const int w = (int)((ptr[sl + 1] - base) >> 5);
+        if (i >= n) {                               // rows past the end of the last slice
+            for (int k = 0; k < w; ++k) { sci[base + 32 * k + r] = 0; sv[base + 32 * k + r] = 0.0; }
+            continue;
+        }
+        const int b = rp[i], len = rp[i + 1] - b;
+        for (int k = 0; k < w; ++k) {
+            const int64_t e = base + 32 * (int64_t)k + r;
+            if (k < len) { sci[e] = ci[b + k]; sv[e] = v[b + k]; }
+            else { sci[e] = i; sv[e] = 0.0; }
+        }
+    }
+}
+
+__global__ void k_widths_to_sizes(const int *w, int nslices, int64_t *sz) {
+    for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += gridDim.x * blockDim.x)
+        sz[sl] = 32 * (int64_t)w[sl];
+}
+
+void build_sell(const DCsr &A, const double *vals, Sell &S, cudaStream_t s) {
+    S.n = A.n;
+    S.nslices = (A.n + 31) / 32;
+    DBuf<int> w(S.nslices);
+    k_sell_width<<<grid_for(S.nslices, 256), 256, 0, s>>>(A.n, A.rp.get(), S.nslices, w.get());
+    CU_LAUNCH("k_sell_width"); count_launch();
+    std::vector<int> hw(S.nslices);
+    CU(cudaMemcpyAsync(hw.data(), w.get(), sizeof(int) * S.nslices, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    std::vector<int64_t> hp(S.nslices + 1, 0);
+    for (int sl = 0; sl < S.nslices; ++sl) hp[sl + 1] = hp[sl] + 32 * (int64_t)hw[sl];
+    S.padded = hp[S.nslices];
+    S.ptr.alloc(S.nslices + 1);
+    CU(cudaMemcpyAsync(S.ptr.get(), hp.data(), sizeof(int64_t) * (S.nslices + 1), cudaMemcpyHostToDevice, s));
+    S.ci.alloc(S.padded > 0 ? S.padded : 1);
+    S.v.alloc(S.padded > 0 ? S.padded : 1);
+    k_sell_fill<<<grid_for((size_t)S.nslices * 32, 256), 256, 0, s>>>(A.n, A.rp.get(), A.ci.get(), vals, S.ptr.get(),
+                                                                      S.ci.get(), S.v.get());
+    CU_LAUNCH("k_sell_fill"); count_launch();
+    CU(cudaStreamSynchronize(s));
 }
 
 // ------------------------------------------------------------------ casts

@@ -22,6 +22,14 @@ template <> __device__ __forceinline__ double val_as<double, float>(float x) { r
 
 template <typename T, typename U> __device__ __forceinline__ T cvt(U x) { return (T)x; }
 
+// acc - a*b and acc + a*b.  In FP64 the product and the sum are rounded
+// separately (no fused multiply-add), which is how the plain sequential
+// definition rounds; the FP32/BF16 V-cycle keeps the fused form.
+__device__ __forceinline__ double msub(double acc, double a, double b) { return __dsub_rn(acc, __dmul_rn(a, b)); }
+__device__ __forceinline__ float msub(float acc, float a, float b) { return acc - a * b; }
+__device__ __forceinline__ double madd(double acc, double a, double b) { return __dadd_rn(acc, __dmul_rn(a, b)); }
+__device__ __forceinline__ float madd(float acc, float a, float b) { return acc + a * b; }
+
 // ------------------------------------------------------------------ CSR SpMV / residual
 // G lanes per row; lanes stride the row, then a shuffle tree reduction.
 // mode 0: y = A x;  mode 1: y = b - A x.
@@ -72,9 +80,53 @@ void residual_f64(int n, int nnz, const int *rp, const int *ci, const double *v,
     spmv_t<double, double, double, double>(n, nnz, rp, ci, v, x, b, r, 1, s);
 }
 
+template <typename XT>
+__global__ void __launch_bounds__(256) k_sell_spmv(int n, const int64_t *__restrict__ ptr, const int *__restrict__ ci,
+                                                   const double *__restrict__ v, const XT *__restrict__ x,
+                                                   const double *__restrict__ b, double *__restrict__ y, int mode) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int sl = i >> 5, r = i & 31;
+        const int64_t base = ptr[sl];
+        const int w = (int)((ptr[sl + 1] - base) >> 5);
+        const double *vv = v + base + r;
+        const int *cc = ci + base + r;
+        double acc = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < w; ++k) acc = madd(acc, __ldg(vv + 32 * k), (double)__ldg(x + __ldg(cc + 32 * k)));
+        y[i] = mode ? b[i] - acc : acc;
+    }
+}
+
+template <typename XT>
+void sell_spmv(int n, int nslices, const int64_t *ptr, const int *ci, const double *v, const XT *x, const double *b,
+               double *y, int mode, cudaStream_t s) {
+    (void)nslices;
+    k_sell_spmv<XT><<<grid_for(n, 256), 256, 0, s>>>(n, ptr, ci, v, x, b, y, mode);
+    CU_LAUNCH("k_sell_spmv"); count_launch();
+}
+template void sell_spmv<double>(int, int, const int64_t *, const int *, const double *, const double *, const double *,
+                                double *, int, cudaStream_t);
+template void sell_spmv<float>(int, int, const int64_t *, const int *, const double *, const float *, const double *,
+                               double *, int, cudaStream_t);
+
+// r = b - A x, one thread per row, terms summed in stored column order.
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) k_residual_seq(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                      const V *__restrict__ v, const T *__restrict__ x,
+                                                      const T *__restrict__ b, T *__restrict__ r) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T acc = 0;
+        const int e1 = rp[i + 1];
+        for (int e = rp[i]; e < e1; ++e) acc = madd(acc, val_as<T, V>(v[e]), x[ci[e]]);
+        r[i] = b[i] - acc;
+    }
+}
+
 template <typename T, typename V>
 void level_residual(const LevelMats<V> &M, const T *x, const T *b, T *r, cudaStream_t s) {
-    spmv_t<V, T, T, T>(M.n, M.nnz, M.rp, M.ci, M.v, x, b, r, 1, s);
+    if (M.n <= 0) return;
+    k_residual_seq<T, V><<<grid_for(M.n, 256), 256, 0, s>>>(M.n, M.rp, M.ci, M.v, x, b, r);
+    CU_LAUNCH("k_residual_seq"); count_launch();
 }
 template void level_residual<double, double>(const LevelMats<double> &, const double *, const double *, double *, cudaStream_t);
 template void level_residual<float, float>(const LevelMats<float> &, const float *, const float *, float *, cudaStream_t);
@@ -94,7 +146,7 @@ __global__ void __launch_bounds__(128) k_sweep(int cnt, const int *__restrict__ 
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         const int i = rows[t];
         T acc = in[i];
-        for (int e = rp[t]; e < rp[t + 1]; ++e) acc -= val_as<T, V>(v[e]) * out[ci[e]];
+        for (int e = rp[t]; e < rp[t + 1]; ++e) acc = msub(acc, val_as<T, V>(v[e]), out[ci[e]]);
         out[i] = with_diag ? acc / dg[t] : acc;
     }
 }
@@ -199,8 +251,8 @@ __device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, int with_d
             T acc = in_coherent ? ld_cg(in + pi) : pin;
 #pragma unroll
             for (int q = 0; q < SWEEP_PF; ++q)
-                if (pk0 + q < pk1) acc -= val_as<T, V>(pv[q]) * ld_cg(out + pc[q]);
-            for (int k = pk0 + SWEEP_PF; k < pk1; ++k) acc -= val_as<T, V>(S.v[k]) * ld_cg(out + S.ci[k]);
+                if (pk0 + q < pk1) acc = msub(acc, val_as<T, V>(pv[q]), ld_cg(out + pc[q]));
+            for (int k = pk0 + SWEEP_PF; k < pk1; ++k) acc = msub(acc, val_as<T, V>(S.v[k]), ld_cg(out + S.ci[k]));
             out[pi] = with_diag ? acc / pd : acc;
             // further rows of this level owned by this thread (levels wider than the grid)
             const int e = S.dlev[l + 1];
@@ -208,7 +260,7 @@ __device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, int with_d
                 const int i = S.rows[t];
                 T a2 = in_coherent ? ld_cg(in + i) : in[i];
                 const int k1 = S.rp[t + 1];
-                for (int k = S.rp[t]; k < k1; ++k) a2 -= val_as<T, V>(S.v[k]) * ld_cg(out + S.ci[k]);
+                for (int k = S.rp[t]; k < k1; ++k) a2 = msub(a2, val_as<T, V>(S.v[k]), ld_cg(out + S.ci[k]));
                 out[i] = with_diag ? a2 / S.d[t] : a2;
             }
         }
@@ -228,12 +280,11 @@ __global__ void __launch_bounds__(256) k_sweep_pair(SweepView<T, V> F, int f_dia
 template <typename T, typename V>
 void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
                      T *y, T *out, unsigned int *bar, int *err, cudaStream_t s) {
-    static int grid = 0;
-    if (!grid) {
+    static const int grid = [] {               // initialised once, thread-safe
         int per_sm = 0;
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_pair<T, V>, 256, 0));
-        grid = sm_count() * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
-    }
+        return sm_count() * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
+    }();
     int maxw = 0;
     for (int l = 0; l < F.nlev; ++l) maxw = max(maxw, F.lev_ptr[l + 1] - F.lev_ptr[l]);
     for (int l = 0; l < B.nlev; ++l) maxw = max(maxw, B.lev_ptr[l + 1] - B.lev_ptr[l]);
@@ -255,6 +306,230 @@ template void sweep_pair_coop<float, __nv_bfloat16>(const SweepView<float, __nv_
                                                     float *, unsigned int *, int *, cudaStream_t);
 template void sweep<float, float>(const SweepView<float, float> &, const float *, float *, int, cudaStream_t);
 template void sweep<float, __nv_bfloat16>(const SweepView<float, __nv_bfloat16> &, const float *, float *, int, cudaStream_t);
+
+// ------------------------------------------------------------------ dataflow sweeps
+// The same triangular solves without level barriers.  Rows are taken in the
+// schedule order (a topological order of the solve's dependencies); each
+// thread owns positions tid, tid + nthr, ... and a row starts as soon as the
+// values it reads are there.  Readiness is carried by the value itself: the
+// output vector holds a signalling-NaN sentinel until the row is written, and
+// arithmetic never yields that bit pattern (a computed NaN is the quiet
+// canonical one; a stored value equal to the sentinel is replaced by it).
+// Each aligned 32/64-bit store and load is single-copy atomic, so a reader
+// sees either the sentinel or the final value.  The terms of a row are
+// consumed in stored order, so the result is the one of the level-by-level
+// sweep bit for bit.
+//
+// Progress: all blocks are resident (cooperative launch) and a warp polls
+// with every lane in one loop, so the lowest unfinished position always has
+// its inputs and an owner that is not blocked: the solve cannot deadlock.
+// Every wait is still bounded (DF_SPIN_LIMIT polls per row); on expiry the
+// kernel sets *err and all threads leave.
+//
+// Sentinel upkeep: y (the forward result) is sentinel on entry and is put back
+// to sentinel row by row as the backward solve consumes it; out is reset to
+// sentinel during the forward solve and a grid barrier separates that reset
+// from the backward solve.
+constexpr unsigned int DF_SPIN_LIMIT = 1u << 20;
+
+template <typename T> struct Sentinel;
+template <> struct Sentinel<float> {
+    static __device__ __forceinline__ unsigned int bits() { return 0x7fa5a5a5u; }
+    static __device__ __forceinline__ bool is(float x) { return __float_as_uint(x) == bits(); }
+    static __device__ __forceinline__ float value() { return __uint_as_float(bits()); }
+    static __device__ __forceinline__ float ld(const float *p) {
+        unsigned int u;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(u) : "l"(p) : "memory");
+        return __uint_as_float(u);
+    }
+    static __device__ __forceinline__ void st(float *p, float x) {
+        unsigned int u = __float_as_uint(x);
+        if (u == bits()) u = 0x7fffffffu;
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(u) : "memory");
+    }
+};
+template <> struct Sentinel<double> {
+    static __device__ __forceinline__ unsigned long long bits() { return 0x7ff4a5a5a5a5a5a5ull; }
+    static __device__ __forceinline__ bool is(double x) { return (unsigned long long)__double_as_longlong(x) == bits(); }
+    static __device__ __forceinline__ double value() { return __longlong_as_double((long long)bits()); }
+    static __device__ __forceinline__ double ld(const double *p) {
+        unsigned long long u;
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(u) : "l"(p) : "memory");
+        return __longlong_as_double((long long)u);
+    }
+    static __device__ __forceinline__ void st(double *p, double x) {
+        unsigned long long u = (unsigned long long)__double_as_longlong(x);
+        if (u == bits()) u = 0x7fffffffffffffffull;
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(u) : "memory");
+    }
+};
+
+template <typename T>
+__global__ void k_fill_sentinel(size_t n, T *x) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = Sentinel<T>::value();
+}
+
+// One triangular solve in dataflow order.  Returns false when a wait ran out
+// or another thread reported one.
+template <typename T, typename V>
+__device__ __forceinline__ bool df_phase(const SweepView<T, V> &S, int with_diag, const T *in, bool in_coherent,
+                                         T *out, T *consumed, int *err, int tid, int nthr) {
+    const int total = S.dlev[S.nlev];
+    const int lane = threadIdx.x & 31;
+    for (int base = tid - lane; base < total; base += nthr) {
+        const int p = base + lane;
+        bool done = p >= total;
+        int i = 0, k = 0, k1 = 0;
+        T acc = T(0), d = T(1);
+        if (!done) {
+            i = S.rows[p];
+            k = S.rp[p];
+            k1 = S.rp[p + 1];
+            acc = in_coherent ? ld_cg(in + i) : in[i];
+            if (with_diag) d = S.d[p];
+        }
+        unsigned int spins = 0;
+        bool fail = false;
+        while (__any_sync(0xffffffffu, !done)) {
+            if (!done) {
+                for (; k < k1; ++k) {
+                    const T xv = Sentinel<T>::ld(out + S.ci[k]);
+                    if (Sentinel<T>::is(xv)) break;
+                    acc = msub(acc, val_as<T, V>(S.v[k]), xv);
+                }
+                if (k == k1) {
+                    Sentinel<T>::st(out + i, with_diag ? acc / d : acc);
+                    if (consumed) consumed[i] = Sentinel<T>::value();
+                    done = true;
+                } else if (++spins > DF_SPIN_LIMIT) {
+                    atomicExch(err, 1);
+                    fail = true;
+                    done = true;
+                } else if ((spins & 255u) == 0 && *(volatile int *)err) {
+                    fail = true;
+                    done = true;
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, fail)) return false;
+    }
+    return true;
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) k_sweep_df(SweepView<T, V> F, int f_diag, SweepView<T, V> B, int b_diag,
+                                                  const T *in, T *y, T *out, unsigned int *bar, int *err) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    const int nb = B.dlev[B.nlev];
+    for (int p = tid; p < nb; p += nthr) out[B.rows[p]] = Sentinel<T>::value();
+    df_phase<T, V>(F, f_diag, in, false, y, nullptr, err, tid, nthr);
+    grid_barrier(bar, err);
+    if (*(volatile int *)err) return;
+    df_phase<T, V>(B, b_diag, y, true, out, y, err, tid, nthr);
+}
+
+template <typename T>
+void fill_sentinel(T *x, size_t n, cudaStream_t s) {
+    if (!n) return;
+    k_fill_sentinel<T><<<grid_for(n, 256), 256, 0, s>>>(n, x);
+    CU_LAUNCH("k_fill_sentinel"); count_launch();
+}
+template void fill_sentinel<float>(float *, size_t, cudaStream_t);
+template void fill_sentinel<double>(double *, size_t, cudaStream_t);
+
+template <typename T, typename V>
+void sweep_pair_df(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in, T *y,
+                   T *out, unsigned int *bar, int *err, cudaStream_t s) {
+    static const int grid = [] {               // initialised once, thread-safe
+        int per_sm = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_df<T, V>, 256, 0));
+        return sm_count() * (per_sm < 1 ? 1 : per_sm);
+    }();
+    const int rows = std::max(F.lev_ptr[F.nlev], B.lev_ptr[B.nlev]);
+    int g = (rows + 255) / 256;
+    if (g > grid) g = grid;
+    if (g < 1) g = 1;
+    SweepView<T, V> f = F, b = B;
+    void *args[] = {&f, (void *)&f_diag, &b, (void *)&b_diag, (void *)&in, (void *)&y, (void *)&out, (void *)&bar,
+                    (void *)&err};
+    CU(cudaLaunchCooperativeKernel((const void *)k_sweep_df<T, V>, dim3(g), dim3(256), args, 0, s));
+    count_launch();
+}
+template void sweep_pair_df<double, double>(const SweepView<double, double> &, int, const SweepView<double, double> &,
+                                            int, const double *, double *, double *, unsigned int *, int *, cudaStream_t);
+template void sweep_pair_df<float, float>(const SweepView<float, float> &, int, const SweepView<float, float> &, int,
+                                          const float *, float *, float *, unsigned int *, int *, cudaStream_t);
+template void sweep_pair_df<float, __nv_bfloat16>(const SweepView<float, __nv_bfloat16> &, int,
+                                                  const SweepView<float, __nv_bfloat16> &, int, const float *, float *,
+                                                  float *, unsigned int *, int *, cudaStream_t);
+
+// ------------------------------------------------------------------ single-block deep V-cycle
+template <typename T, typename V>
+__device__ __forceinline__ void block_sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag) {
+    for (int l = 0; l < S.nlev; ++l) {
+        const int b = S.dlev[l], e = S.dlev[l + 1];
+        for (int t = b + threadIdx.x; t < e; t += blockDim.x) {
+            const int i = S.rows[t];
+            T acc = in[i];
+            const int k1 = S.rp[t + 1];
+            for (int k = S.rp[t]; k < k1; ++k) acc = msub(acc, val_as<T, V>(S.v[k]), out[S.ci[k]]);
+            out[i] = with_diag ? acc / S.d[t] : acc;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(1024) k_deep_vcycle(const DeepLevel<T, V> *L, int count) {
+    int m = 0;
+    for (; m < count; ++m) {
+        const DeepLevel<T, V> &D = L[m];
+        if (D.dense) {                       // exact solve of the last level
+            for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
+                double acc = 0.0;
+                const double *row = D.inv + (size_t)i * D.n;
+                for (int j = 0; j < D.n; ++j) acc += row[j] * (double)D.h[j];
+                D.g[i] = (T)acc;
+            }
+            __syncthreads();
+            break;
+        }
+        block_sweep<T, V>(D.fwd, D.h, D.y, 0);
+        block_sweep<T, V>(D.bwd, D.y, D.has_child ? D.t : D.g, 1);
+        if (!D.has_child) break;
+        for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
+            T acc = 0;
+            const int e1 = D.rp[i + 1];
+            for (int e = D.rp[i]; e < e1; ++e) acc += val_as<T, V>(D.v[e]) * D.t[D.ci[e]];
+            D.r[i] = D.h[i] - acc;
+        }
+        __syncthreads();
+        const DeepLevel<T, V> &C = L[m + 1];
+        for (int I = threadIdx.x; I < C.n; I += blockDim.x) {
+            T acc = 0;
+            for (int q = D.mptr[I]; q < D.mptr[I + 1]; ++q) acc += D.r[D.midx[q]];
+            C.h[I] = acc;
+        }
+        __syncthreads();
+    }
+    for (int k = (m < count ? m : count - 1) - 1; k >= 0; --k) {
+        const DeepLevel<T, V> &D = L[k];
+        const DeepLevel<T, V> &C = L[k + 1];
+        for (int i = threadIdx.x; i < D.n; i += blockDim.x) D.g[i] = D.t[i] + C.g[D.agg[i]];
+        __syncthreads();
+    }
+}
+
+template <typename T, typename V>
+void deep_vcycle(const DeepLevel<T, V> *levels, int count, cudaStream_t s) {
+    k_deep_vcycle<T, V><<<1, 1024, 0, s>>>(levels, count);
+    CU_LAUNCH("k_deep_vcycle");
+    count_launch();
+}
+template void deep_vcycle<double, double>(const DeepLevel<double, double> *, int, cudaStream_t);
+template void deep_vcycle<float, float>(const DeepLevel<float, float> *, int, cudaStream_t);
+template void deep_vcycle<float, __nv_bfloat16>(const DeepLevel<float, __nv_bfloat16> *, int, cudaStream_t);
 
 // ------------------------------------------------------------------ transfers
 // h[I] = sum over members m of I (ascending) of r[m]  (restriction P^T)
@@ -323,23 +598,21 @@ void convert_f32_f64(size_t n, const float *in, double *out, cudaStream_t s) {
     CU_LAUNCH("k_convert"); count_launch();
 }
 
-// Dense last level: g = Ainv h (transpose: g = Ainv^T h); one warp per row.
+// Dense last level: g = Ainv h (transpose: g = Ainv^T h); one thread per
+// row, the row's terms summed in column order.
 template <typename T>
 __global__ void k_dense_gemv(int n, const double *__restrict__ inv, const T *__restrict__ h, T *__restrict__ g,
                              int transpose, int mode) {
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * blockDim.x / 32;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / 32; i < n; i += warps) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int j = lane; j < n; j += 32)
-            acc += (transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j]) * (double)h[j];
-        for (int off = 16; off; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-        if (lane == 0) g[i] = mode ? (T)((double)g[i] + acc) : (T)acc;
+        for (int j = 0; j < n; ++j)
+            acc = madd(acc, transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j], (double)h[j]);
+        g[i] = mode ? (T)((double)g[i] + acc) : (T)acc;
     }
 }
 template <typename T>
 void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, cudaStream_t s) {
-    k_dense_gemv<T><<<grid_for((size_t)n * 32, 256), 256, 0, s>>>(n, inv, h, g, transpose, mode);
+    k_dense_gemv<T><<<grid_for((size_t)n, 64), 64, 0, s>>>(n, inv, h, g, transpose, mode);
     CU_LAUNCH("k_dense_gemv"); count_launch();
 }
 template void dense_solve<double>(int, const double *, const double *, double *, int, int, cudaStream_t);
@@ -451,24 +724,29 @@ __global__ void __launch_bounds__(RT) k_cgs_update(size_t n, const FgState *st, 
 }
 
 // Givens step for column j (single thread): H column from h1 + h2 and ||w||,
-// apply previous rotations, new rotation, residual estimate.
+// apply previous rotations, new rotation, residual estimate.  Products and
+// sums are rounded one by one (no fused multiply-add), as in the plain
+// sequential statement of the rotations.
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+
 __global__ void k_givens(FgState *st) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (st->stop) return;
     const int m = st->m;
     const int j = st->j;
     double *H = st->H;                       // H[k*m + j]
-    for (int k = 0; k <= j; ++k) H[k * m + j] = st->h1[k] + st->h2[k];
+    for (int k = 0; k <= j; ++k) H[k * m + j] = add(st->h1[k], st->h2[k]);
     const double hn = sqrt(st->nrm2[0]);
     H[(j + 1) * m + j] = hn;
-    st->inv_hn = hn != 0.0 ? 1.0 / hn : 0.0;
+    st->hn = hn;
     for (int k = 0; k < j; ++k) {
         double a = H[k * m + j], c = H[(k + 1) * m + j];
-        H[k * m + j] = st->cs[k] * a + st->sn[k] * c;
-        H[(k + 1) * m + j] = -st->sn[k] * a + st->cs[k] * c;
+        H[k * m + j] = add(mul(st->cs[k], a), mul(st->sn[k], c));
+        H[(k + 1) * m + j] = add(mul(-st->sn[k], a), mul(st->cs[k], c));
     }
     double a = H[j * m + j], c = H[(j + 1) * m + j];
-    double rho = sqrt(a * a + c * c);
+    double rho = sqrt(add(mul(a, a), mul(c, c)));
     if (!(rho > 0.0) || !isfinite(rho)) {
         st->status = 6;
         st->stop = 1;
@@ -478,8 +756,8 @@ __global__ void k_givens(FgState *st) {
     st->sn[j] = c / rho;
     H[j * m + j] = rho;
     H[(j + 1) * m + j] = 0.0;
-    st->s[j + 1] = -st->sn[j] * st->s[j];
-    st->s[j] = st->cs[j] * st->s[j];
+    st->s[j + 1] = mul(-st->sn[j], st->s[j]);
+    st->s[j] = mul(st->cs[j], st->s[j]);
     st->total += 1;
     const double est = fabs(st->s[j + 1]) / st->bnorm;
     if (st->hist_len < st->hist_cap) st->hist[st->hist_len++] = est;
@@ -489,14 +767,15 @@ __global__ void k_givens(FgState *st) {
     if (est <= st->tol || hn == 0.0 || st->total >= st->maxit || j + 1 >= m) st->stop = 1;
 }
 
-// V_{j} = w * inv_hn after the Givens step advanced j (skipped at the last column)
+// V_{j} = w / h_{j,j-1} after the Givens step advanced j (skipped at the last
+// column and when w vanished)
 __global__ void k_scale_next(size_t n, const double *__restrict__ w, double *__restrict__ V, const FgState *st) {
     const int j = st->j;
-    if (j > st->m) return;
+    const double hn = st->hn;
+    if (j > st->m || hn == 0.0) return;
     double *vout = V + (size_t)j * n;
-    const double a = st->inv_hn;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        vout[i] = w[i] * a;
+        vout[i] = w[i] / hn;
 }
 
 template <typename T>
@@ -533,7 +812,7 @@ __global__ void k_backsolve(FgState *st) {
     const int m = st->m, j = st->jdone;
     for (int k = j - 1; k >= 0; --k) {
         double t = st->s[k];
-        for (int l = k + 1; l < j; ++l) t -= st->H[k * m + l] * st->y[l];
+        for (int l = k + 1; l < j; ++l) t = __dsub_rn(t, __dmul_rn(st->H[k * m + l], st->y[l]));
         st->y[k] = t / st->H[k * m + k];
     }
 }
@@ -547,7 +826,7 @@ __global__ void k_update_x(size_t n, const FgState *st, const ZT *__restrict__ Z
     __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double acc = x[i];
-        for (int k = 0; k < j; ++k) acc += ys[k] * (double)Z[k * ldz + i];
+        for (int k = 0; k < j; ++k) acc = __dadd_rn(acc, __dmul_rn(ys[k], (double)Z[k * ldz + i]));
         x[i] = acc;
     }
 }
@@ -571,7 +850,89 @@ __global__ void __launch_bounds__(RT) k_norm2(size_t n, const double *__restrict
     }
 }
 
-int reduce_grid() { return sm_count() * 2; }
+// Modified Gram-Schmidt step of the Arnoldi process, the form of the plain
+// sequential definition: for k = 0..j, h_k = (w, v_k) then w <- w - h_k v_k;
+// finally ||w||^2.  One cooperative launch; the update of step k is fused
+// with the dot product of step k + 1 (or the norm after the last step).  Each
+// block reduces its part, a grid barrier follows, and every block then adds
+// the block partials in block order, so all blocks hold the same h_k.  Step
+// partials alternate between two halves of the buffer: a block still reading
+// step k's partials cannot be overtaken by writes of step k + 2, which lie
+// behind the barrier of step k + 1.  Products and sums are rounded one by
+// one (no fused multiply-add).  Each element of w is touched by one thread
+// only, so w needs no cross-block visibility.
+__device__ __forceinline__ double mgs_grid_sum(double acc, double *partials, unsigned int *bar, int *err) {
+    __shared__ double red[RT / 32];
+    __shared__ double total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int off = 16; off; off >>= 1) acc = __dadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, off));
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < RT / 32; ++w) a = __dadd_rn(a, red[w]);
+        __stcg(partials + blockIdx.x, a);
+    }
+    grid_barrier(bar, err);
+    if (warp == 0) {
+        double a = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) a = __dadd_rn(a, __ldcg(partials + b));
+        for (int off = 16; off; off >>= 1) a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, off));
+        if (lane == 0) total = a;
+    }
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(RT) k_mgs(size_t n, FgState *st, double *w, const double *__restrict__ V,
+                                            size_t ldv, double *partials, unsigned int *bar, int *err) {
+    if (st->stop) return;                    // same value in every block
+    const int j = st->j;
+    const size_t tid = blockIdx.x * (size_t)RT + threadIdx.x, nthr = (size_t)gridDim.x * RT;
+    double acc = 0.0;
+    for (size_t i = tid; i < n; i += nthr) acc = __dadd_rn(acc, __dmul_rn(w[i], V[i]));
+    double h = mgs_grid_sum(acc, partials, bar, err);
+    for (int k = 0; k <= j; ++k) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) { st->h1[k] = h; st->h2[k] = 0.0; }
+        const double *vk = V + (size_t)k * ldv;
+        const double *vn = V + (size_t)(k + 1) * ldv;
+        acc = 0.0;
+        if (k < j) {
+            for (size_t i = tid; i < n; i += nthr) {
+                const double wi = __dsub_rn(w[i], __dmul_rn(h, vk[i]));
+                w[i] = wi;
+                acc = __dadd_rn(acc, __dmul_rn(wi, vn[i]));
+            }
+        } else {
+            for (size_t i = tid; i < n; i += nthr) {
+                const double wi = __dsub_rn(w[i], __dmul_rn(h, vk[i]));
+                w[i] = wi;
+                acc = __dadd_rn(acc, __dmul_rn(wi, wi));
+            }
+        }
+        h = mgs_grid_sum(acc, partials + (size_t)((k + 1) & 1) * gridDim.x, bar, err);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->nrm2[0] = h;
+}
+
+void mgs(size_t n, FgState *st, double *w, const double *V, size_t ldv, double *partials, unsigned int *bar,
+         int *err, cudaStream_t s) {
+    static const int grid = [] {               // initialised once, thread-safe
+        int per_sm = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgs, RT, 0));
+        const int g = sm_count() * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
+        return std::min(g, reduce_grid() * KMAX1 / 2);   // two halves of the partials buffer
+    }();
+    size_t g = (n + RT - 1) / RT;
+    if (g > (size_t)grid) g = grid;
+    if (g < 1) g = 1;
+    void *args[] = {(void *)&n, (void *)&st, (void *)&w, (void *)&V, (void *)&ldv, (void *)&partials, (void *)&bar,
+                    (void *)&err};
+    CU(cudaLaunchCooperativeKernel((const void *)k_mgs, dim3((unsigned)g), dim3(RT), args, 0, s));
+    count_launch();
+}
+
+int reduce_grid() { return sm_count() * 4; }
 
 void mdot(size_t n, const FgState *st, const double *w, const double *V, size_t ldv, double *partials,
           unsigned int *ticket, double *h, cudaStream_t s) {
@@ -603,9 +964,9 @@ void backsolve(FgState *st, cudaStream_t s) {
 // restart: V_0 = r / beta with beta = sqrt(nrm2); s = beta e1
 __global__ void k_restart_scale(size_t n, const double *__restrict__ r, double *__restrict__ v0, FgState *st) {
     const double beta = sqrt(st->nrm2[0]);
-    const double a = beta > 0.0 ? 1.0 / beta : 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        v0[i] = r[i] * a;
+    if (beta > 0.0)
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+            v0[i] = r[i] / beta;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int k = 0; k <= st->m; ++k) st->s[k] = 0.0;
         st->s[0] = beta;

@@ -15,7 +15,7 @@ constexpr int KMAX1 = 32;
 struct FgState {
     int m, maxit, total, hist_len, hist_cap, jdone, stop, status;
     int j, pad_i;                           // current inner column
-    double tol, bnorm, inv_hn, pad;
+    double tol, bnorm, hn, pad;           // hn = h_{j+1,j} of the last column
     double H[(KMAX1 + 1) * KMAX1];
     double cs[KMAX1], sn[KMAX1], s[KMAX1 + 1], y[KMAX1];
     double h1[KMAX1 + 1], h2[KMAX1 + 1], nrm2[2];
@@ -46,6 +46,12 @@ void spmv_f64_xf32(int n, int nnz, const int *rp, const int *ci, const double *v
 void residual_f64(int n, int nnz, const int *rp, const int *ci, const double *v, const double *x, const double *b,
                   double *r, cudaStream_t s);
 
+// y = A x (mode 0) or y = b - A x (mode 1) on the SELL-32 copy; each row is
+// summed sequentially in column order.
+template <typename XT>
+void sell_spmv(int n, int nslices, const int64_t *ptr, const int *ci, const double *v, const XT *x, const double *b,
+               double *y, int mode, cudaStream_t s);
+
 template <typename T, typename V>
 void level_residual(const LevelMats<V> &M, const T *x, const T *b, T *r, cudaStream_t s);
 template <typename T, typename V>
@@ -57,6 +63,10 @@ void sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag, cudaStr
 template <typename T, typename V>
 void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
                      T *y, T *out, unsigned int *bar, int *err, cudaStream_t s);
+template <typename T, typename V>
+void sweep_pair_df(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in, T *y,
+                   T *out, unsigned int *bar, int *err, cudaStream_t s);
+template <typename T> void fill_sentinel(T *x, size_t n, cudaStream_t s);
 template <typename T>
 void restrict_to(int nc, const int *mptr, const int *midx, const T *r, T *h, cudaStream_t s);
 template <typename T, typename Q>
@@ -69,8 +79,34 @@ template <typename T>
 void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, cudaStream_t s);
 
 // K = st->j + 1 basis vectors (read on the device)
+// Smoothers with more schedule levels than this (forward + backward) run as
+// one cooperative launch when the persistent option is on.
+constexpr int PERSISTENT_MIN_LEVELS = 16;
+
+// One level of the single-block V-cycle (deep levels, one Richardson step
+// per level): g_m = S_m^{-1} h_m + P g_{m+1}, h_{m+1} = P^T (h_m - A_m S_m^{-1} h_m);
+// the last level is solved by its dense inverse or by S^{-1} alone.
+template <typename T, typename V>
+struct DeepLevel {
+    int n, dense, has_child, pad;
+    const int *rp, *ci;
+    const V *v;
+    SweepView<T, V> fwd, bwd;
+    const double *inv;
+    const int *agg, *mptr, *midx;
+    T *h, *g, *t, *y, *r;
+};
+
+template <typename T, typename V>
+void deep_vcycle(const DeepLevel<T, V> *levels, int count, cudaStream_t s);
+
 void mdot(size_t n, const FgState *st, const double *w, const double *V, size_t ldv, double *partials,
           unsigned int *ticket, double *h, cudaStream_t s);
+// Modified Gram-Schmidt for column j = st->j in one cooperative launch:
+// h1[k] = (w, v_k) with w updated after each k, h2[k] = 0, nrm2[0] = ||w||^2.
+// partials: >= 2 x grid doubles; bar/err as for the sweeps.
+void mgs(size_t n, FgState *st, double *w, const double *V, size_t ldv, double *partials, unsigned int *bar,
+         int *err, cudaStream_t s);
 void cgs_update(size_t n, const FgState *st, const double *hin, double *w, const double *V, size_t ldv,
                 int want_dots, double *partials, unsigned int *ticket, double *hout, cudaStream_t s);
 // zin = V_{st->j} (FP64 copy or FP32 conversion)
