@@ -279,6 +279,9 @@ def main():
                     help="one setup + solve of the workload (for ncu captures), no timing output")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--bf16-steps", type=int, default=1, help="steps of the BF16-value V-cycle leg (fp32 runs)")
+    ap.add_argument("--fp64-dot2", type=int, default=0, choices=[0, 1],
+                    help="accurate (Dot2) inner products in the all-FP64 comparison leg (0: plain, as the mixed leg)")
     ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2],
                     help="ILU(0) sweep schedule: 0 per-level launches, 1 level barriers, 2 dataflow")
     ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
@@ -319,7 +322,10 @@ def main():
             opts[k] = getattr(args, k)
 
     def step(prec, timing_class=0, acc=None):
-        h = amg.amg_setup(A, vcycle_prec=prec, **opts)
+        o = dict(opts)
+        if prec == amg.AMG_FP64 and vp != amg.AMG_FP64:
+            o.setdefault("dot2", args.fp64_dot2)      # the all-FP64 comparison leg
+        h = amg.amg_setup(A, vcycle_prec=prec, **o)
         if timing_class:
             amg.amg_set_kernel_timing(h, timing_class)
         x = torch.zeros_like(b)
@@ -364,6 +370,11 @@ def main():
     clocks = clk.summary()
     ms64, stats64, acc64, _ = (timed(amg.AMG_FP64, timing_class=1, steps=args.fp64_steps) if vp != amg.AMG_FP64
                                else (ms, stats, [], None))
+    bf16 = None
+    if args.prec == "fp32" and args.bf16_steps > 0:
+        ms16, stats16, _, _ = timed(amg.AMG_BF16, steps=args.bf16_steps)
+        bf16 = {"ms_per_step": round(ms16, 2), "iters": stats16[-1].iters,
+                "rel_res_true": stats16[-1].rel_res_true, "speedup_vs_fp64": round(ms64 / ms16, 3)}
 
     # end to end through the C ABI with host buffers (copies inside the region)
     Ah = amg.CsrDevice(A.n, A.row_ptr.cpu().numpy(), A.col.cpu().numpy(), A.val.cpu().numpy())
@@ -415,7 +426,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iters": s0.iters, "rel_res_true": s0.rel_res_true, "setup_ms": round(s0.setup_ms, 2),
         "solve_ms": round(s0.solve_ms, 2), "fp64_ms_per_step": round(ms64, 2), "fp64_iters": stats64[-1].iters,
-        "speedup_vs_fp64": round(ms64 / ms, 3), "levels": s0.nlevels,
+        "speedup_vs_fp64": round(ms64 / ms, 3), "fp64_dot2": args.fp64_dot2, "bf16_vcycle": bf16, "levels": s0.nlevels,
         "e2e": {"value": round(statistics.median(e2e), 2), "unit": "ms", "h2d_bytes_per_step": int(bi),
                 "d2h_bytes_per_step": int(bo)},
         "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "spmv_roofline": spmv_roof,

@@ -132,6 +132,18 @@ typedef struct {
                                  column) or AMG_ORTHO_CGS2 (classical
                                  Gram-Schmidt with one re-orthogonalisation
                                  pass): AMG_ORTHO_MGS                      */
+    int32_t spmv_block;       /* threads per block of the outer FP64 SpMV:
+                                 64/128/256/512, or 0 = autotuned at setup */
+    int32_t spmv_unroll;      /* unroll depth of its column loop: 2/4/8, or
+                                 0 = autotuned at setup.  Neither changes
+                                 the result (rows are summed in the same
+                                 order by every variant): 0                 */
+    int32_t dot2;             /* Arnoldi inner products and norms as if in
+                                 twice the working precision (Dot2, Ogita-
+                                 Rump-Oishi 2005), independent of the
+                                 reduction order: 1 on, 0 plain FMA sums,
+                                 -1 = on with the FP64 V-cycle only: -1    */
+    int32_t reserved0;        /* 0                                         */
     uint64_t seed;            /* tie-break seed, default 0                 */
 } amg_options_t;
 
@@ -253,6 +265,10 @@ int amg_spmv_noalloc(const amg_csr_t *A, const double *x, double *y, void *strea
  * [7] sweep levels of the backward solve.  info: host [8]. */
 int amg_get_level_info(amg_handle_t *h, int32_t level, int64_t *info);
 int amg_num_levels(amg_handle_t *h, int32_t *nlevels);
+
+/* Launch geometry the outer SpMV of h uses (picked by the autotuner unless
+ * fixed by the options).  No counterpart in the paper.  block, unroll: host. */
+int amg_get_spmv_config(amg_handle_t *h, int32_t *block, int32_t *unroll);
 
 /* Aggregate map of level l: pass 0 = composite map to level l+1 (rows of
  * level l), pass p >= 1 = map of matching pass p.  out: host. */

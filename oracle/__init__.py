@@ -61,6 +61,8 @@ def lib():
             L.or_fv_grad_logk.argtypes = [C.c_int] * 4 + [f64p] * 5 + [f64p] * 3
             L.or_spmv.argtypes = [C.c_int, i64p, i32p, f64p, f64p, f64p]
             L.or_spmv_t.argtypes = [C.c_int, i64p, i32p, f64p, f64p, f64p]
+            L.or_dot.restype = C.c_double
+            L.or_dot.argtypes = [C.c_int, f64p, f64p]
             L.or_check_csr.restype = C.c_int
             L.or_check_csr.argtypes = [C.c_int, i64p, i32p]
             L.or_edge_weight.restype = C.c_double
@@ -183,6 +185,14 @@ def spmv(A, x, transpose=False):
     y = np.zeros(A.n)
     (lib().or_spmv_t if transpose else lib().or_spmv)(A.n, A.row_ptr, A.col, A.val, _f64(x), y)
     return y
+
+
+def dot(a, b) -> float:
+    """Inner product of the Arnoldi process, as if in twice the working
+    precision (Dot2 of Ogita, Rump and Oishi, 2005)."""
+    a, b = _f64(a), _f64(b)
+    assert a.shape == b.shape
+    return float(lib().or_dot(len(a), a, b))
 
 
 def check_csr(A) -> int:

@@ -9,8 +9,13 @@
  * coarse grid solve for algebraic multigrid", arXiv:1105.3468) and from the
  * readings listed with each function.
  *
- * Compiled with -O2 -ffp-contract=off so that every a*b+c rounds twice, as
- * written.
+ * Compiled with -O2 -ffp-contract=off, so an expression a*b+c rounds twice,
+ * as written.  Rounding of multiply-accumulate (the paper does not fix it):
+ * the setup (assembly, gradient, ILU(0) factorisation, dense inverse)
+ * rounds each product and each sum; the solve phase (matrix-vector
+ * products, triangular solves, the dense product, dot products, vector
+ * updates, Givens rotations, back substitution) accumulates with fma(),
+ * IEEE 754 fused multiply-add with a single rounding.
  *
  * Status codes (same numeric meaning as the library's public header, defined
  * independently here):
@@ -207,7 +212,7 @@ void or_spmv(int n, const int64_t *rp, const int32_t *ci, const double *v,
 {
     for (int i = 0; i < n; ++i) {
         double s = 0.0;
-        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) s += v[e] * x[ci[e]];
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) s = fma(v[e], x[ci[e]], s);
         y[i] = s;
     }
 }
@@ -218,7 +223,7 @@ void or_spmv_t(int n, const int64_t *rp, const int32_t *ci, const double *v,
 {
     for (int i = 0; i < n; ++i) y[i] = 0.0;
     for (int i = 0; i < n; ++i)
-        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) y[ci[e]] += v[e] * x[i];
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) y[ci[e]] = fma(v[e], x[i], y[ci[e]]);
 }
 
 static int64_t find_in_row(const int64_t *rp, const int32_t *ci, int row, int32_t c)
@@ -539,14 +544,14 @@ void or_ilu_solve(int n, const int64_t *rp, const int32_t *ci, const double *lu,
         int i = perm[q];
         double s = z[i];
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
-            if (pos[ci[e]] < pos[i]) s -= lu[e] * y[ci[e]];
+            if (pos[ci[e]] < pos[i]) s = fma(-lu[e], y[ci[e]], s);
         y[i] = s;
     }
     for (int q = n - 1; q >= 0; --q) {
         int i = perm[q];
         double s = y[i], d = 0.0;
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
-            if (pos[ci[e]] > pos[i]) s -= lu[e] * t[ci[e]];
+            if (pos[ci[e]] > pos[i]) s = fma(-lu[e], t[ci[e]], s);
             else if (ci[e] == i) d = lu[e];
         }
         t[i] = s / d;
@@ -571,13 +576,13 @@ void or_ilu_solve_t(int n, const int64_t *rp, const int32_t *ci, const double *l
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e) if (ci[e] == i) d = lu[e];
         w[i] = w[i] / d;
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
-            if (pos[ci[e]] > pos[i]) w[ci[e]] -= lu[e] * w[i];
+            if (pos[ci[e]] > pos[i]) w[ci[e]] = fma(-lu[e], w[i], w[ci[e]]);
     }
     for (int i = 0; i < n; ++i) t[i] = w[i];
     for (int q = n - 1; q >= 0; --q) {
         int i = perm[q];
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
-            if (pos[ci[e]] < pos[i]) t[ci[e]] -= lu[e] * t[i];
+            if (pos[ci[e]] < pos[i]) t[ci[e]] = fma(-lu[e], t[i], t[ci[e]]);
     }
     free(perm); free(pos); free(w);
 }
@@ -629,7 +634,7 @@ static void dense_solve(int n, const double *inv, const double *b, double *x, in
 {
     for (int i = 0; i < n; ++i) {
         double s = 0.0;
-        for (int j = 0; j < n; ++j) s += (transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j]) * b[j];
+        for (int j = 0; j < n; ++j) s = fma(transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j], b[j], s);
         x[i] = s;
     }
 }
@@ -965,12 +970,37 @@ void or_precond_t(const or_hier_t *H, const double *z, double *q) { precond_leve
 /* out_i[0] = iterations, out_i[1] = restarts, out_i[2] = hist length.  */
 /* out_d[0] = true final relative residual.                              */
 /* ------------------------------------------------------------------ */
-static double dot(int n, const double *a, const double *b)
+/* Inner products of the Arnoldi process (dot products and norms) are    */
+/* evaluated as if in twice the working precision, by the Dot2 algorithm */
+/* of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26(6), 2005): each     */
+/* product is split exactly into p + e (TwoProduct, via fma), the p are  */
+/* summed with the exact error of every addition kept (TwoSum, Knuth),   */
+/* and the collected errors are added at the end.  Reading: the paper    */
+/* does not fix how inner products are rounded; an accurately rounded    */
+/* value does not depend on the summation order, which a parallel        */
+/* reduction cannot follow.                                              */
+static void two_sum(double a, double b, double *s, double *e)
 {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += a[i] * b[i];
-    return s;
+    double t = a + b;
+    double z = t - a;
+    *e = (a - (t - z)) + (b - z);
+    *s = t;
 }
+
+double or_dot(int n, const double *a, const double *b)
+{
+    double p = 0.0, c = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double h = a[i] * b[i];
+        double r = fma(a[i], b[i], -h);         /* a_i b_i = h + r exactly */
+        double q;
+        two_sum(p, h, &p, &q);
+        c = c + (q + r);
+    }
+    return p + c;
+}
+
+static double dot(int n, const double *a, const double *b) { return or_dot(n, a, b); }
 
 int or_fgmres(const or_hier_t *H, int n, const int64_t *rp, const int32_t *ci, const double *v,
               const double *b, double *x, double tol, int restart, int maxit, int transpose,
@@ -1019,7 +1049,7 @@ int or_fgmres(const or_hier_t *H, int n, const int64_t *rp, const int32_t *ci, c
                 double *vk = V + (size_t)k * n;
                 double hk = dot(n, w, vk);
                 Hm[k * m + j] = hk;
-                for (int i = 0; i < n; ++i) w[i] = w[i] - hk * vk[i];
+                for (int i = 0; i < n; ++i) w[i] = fma(-hk, vk[i], w[i]);
             }
             double hn = sqrt(dot(n, w, w));
             Hm[(j + 1) * m + j] = hn;
@@ -1029,11 +1059,11 @@ int or_fgmres(const or_hier_t *H, int n, const int64_t *rp, const int32_t *ci, c
             }
             for (int k = 0; k < j; ++k) {
                 double a = Hm[k * m + j], c = Hm[(k + 1) * m + j];
-                Hm[k * m + j] = cs[k] * a + sn[k] * c;
-                Hm[(k + 1) * m + j] = -sn[k] * a + cs[k] * c;
+                Hm[k * m + j] = fma(cs[k], a, sn[k] * c);
+                Hm[(k + 1) * m + j] = fma(-sn[k], a, cs[k] * c);
             }
             double a = Hm[j * m + j], c = Hm[(j + 1) * m + j];
-            double rho = sqrt(a * a + c * c);
+            double rho = sqrt(fma(a, a, c * c));
             if (rho == 0.0 || !isfinite(rho)) { status = OR_ENUMERIC; stop = 2; break; }
             cs[j] = a / rho; sn[j] = c / rho;
             Hm[j * m + j] = rho; Hm[(j + 1) * m + j] = 0.0;
@@ -1049,12 +1079,12 @@ int or_fgmres(const or_hier_t *H, int n, const int64_t *rp, const int32_t *ci, c
         /* UPDATE: back-solve the j x j triangle, x += Z y */
         for (int k = j - 1; k >= 0; --k) {
             double t = s[k];
-            for (int l = k + 1; l < j; ++l) t -= Hm[k * m + l] * y[l];
+            for (int l = k + 1; l < j; ++l) t = fma(-Hm[k * m + l], y[l], t);
             y[k] = t / Hm[k * m + k];
         }
         for (int k = 0; k < j; ++k) {
             double *zk = Z + (size_t)k * n;
-            for (int i = 0; i < n; ++i) x[i] = x[i] + y[k] * zk[i];
+            for (int i = 0; i < n; ++i) x[i] = fma(y[k], zk[i], x[i]);
         }
         if (transpose) or_spmv_t(n, rp, ci, v, x, w); else or_spmv(n, rp, ci, v, x, w);
         for (int i = 0; i < n; ++i) w[i] = b[i] - w[i];

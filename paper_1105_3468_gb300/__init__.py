@@ -28,7 +28,7 @@ __all__ = [
     "amg_get_colors", "amg_get_ilu", "amg_fv_assemble", "amg_fv_grad_logk", "amg_version",
     "amg_status_string", "lib", "amg_set_kernel_timing", "amg_get_kernel_timing",
     "amg_launch_counter", "amg_csr_value_grad", "amg_spmv_noalloc", "amg_setup_batched",
-    "amg_solve_batched", "amg_batch_size", "amg_batch_member",
+    "amg_solve_batched", "amg_batch_size", "amg_batch_member", "amg_get_spmv_config",
 ]
 
 
@@ -256,6 +256,13 @@ def amg_get_kernel_timing(h: Handle):
 
 def amg_launch_counter() -> int:
     return int(lib().amg_launch_counter())
+
+
+def amg_get_spmv_config(h: Handle):
+    """amg_get_spmv_config: (threads per block, unroll) of the outer SpMV."""
+    blk, unr = C.c_int32(), C.c_int32()
+    _check(lib().amg_get_spmv_config(h.ptr, C.byref(blk), C.byref(unr)), "amg_get_spmv_config")
+    return blk.value, unr.value
 
 
 def amg_num_levels(h: Handle) -> int:

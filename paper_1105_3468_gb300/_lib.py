@@ -40,7 +40,9 @@ class AmgOptions(C.Structure):
                 ("order_coarse", C.c_int32), ("coloring", C.c_int32), ("restart", C.c_int32),
                 ("maxit", C.c_int32), ("vcycle_prec", C.c_int32), ("build_adjoint", C.c_int32),
                 ("use_graphs", C.c_int32), ("persistent", C.c_int32), ("deep_block_max", C.c_int32),
-                ("orthog", C.c_int32), ("seed", C.c_uint64)]
+                ("orthog", C.c_int32), ("spmv_block", C.c_int32), ("spmv_unroll", C.c_int32),
+                ("dot2", C.c_int32), ("reserved0", C.c_int32),
+                ("seed", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,6 +79,7 @@ SIGNATURES = {
     "amg_spmv_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, _P, _P]),
     "amg_get_level_info": (C.c_int, [_P, C.c_int32, _P]),
     "amg_num_levels": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "amg_get_spmv_config": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "amg_get_aggregates": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),
     "amg_get_matrix": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "amg_get_pass_matrix": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P, _P]),

@@ -6,6 +6,7 @@
 // FGMRES(m) (Algorithm 1, PRECONDITIONED GMRES ITERATION, flexible form).
 #include "../../include/amg.h"
 #include "solve.cuh"
+#include <type_traits>
 
 #include <atomic>
 #include <chrono>
@@ -272,6 +273,60 @@ static void cast_sweep(Sweep &S, int prec, cudaStream_t s) {
 template <typename T, typename V>
 static void build_deep(amg_handle *h);
 
+// SpMV autotuner: times every (threads per block, unroll) pair not fixed by
+// the options on this matrix (one warm-up and three timed launches each, x in
+// the V-cycle's output type) and keeps the fastest.  Results do not depend on
+// the choice.
+static void tune_sell(Sell &SL, const amg_options_t &o, cudaStream_t s) {
+    static const int blocks[] = {64, 128, 256, 512};
+    static const int unrolls[] = {2, 4, 8};
+    SL.block = o.spmv_block ? o.spmv_block : 256;
+    SL.unroll = o.spmv_unroll ? o.spmv_unroll : 4;
+    if (o.spmv_block && o.spmv_unroll) return;
+    const bool f64 = o.vcycle_prec == AMG_FP64;
+    const size_t n = (size_t)SL.n;
+    DBuf<char> xb(n * (f64 ? sizeof(double) : sizeof(float)));
+    DBuf<double> y(n);
+    CU(cudaMemsetAsync(xb.get(), 0, xb.n, s));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bb = SL.block, bu = SL.unroll;
+    try {
+        for (int blk : blocks) {
+            if (o.spmv_block && blk != o.spmv_block) continue;
+            for (int u : unrolls) {
+                if (o.spmv_unroll && u != o.spmv_unroll) continue;
+                auto run = [&] {
+                    if (f64)
+                        sell_spmv<double>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(),
+                                          reinterpret_cast<const double *>(xb.get()), nullptr, y.get(), 0, s, blk, u);
+                    else
+                        sell_spmv<float>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(),
+                                         reinterpret_cast<const float *>(xb.get()), nullptr, y.get(), 0, s, blk, u);
+                };
+                run();
+                CU(cudaEventRecord(e0, s));
+                for (int r = 0; r < 3; ++r) run();
+                CU(cudaEventRecord(e1, s));
+                CU(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CU(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; bb = blk; bu = u; }
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SL.block = bb;
+    SL.unroll = bu;
+}
+
 static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
     const amg_options_t &o = h->opt;
     cudaStream_t s = h->stream;
@@ -305,39 +360,33 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
         }
         if (last) break;
     }
-    // precision copies
-    for (auto &Lp : h->lev) {
-        Level &L = *Lp;
-        if (o.vcycle_prec != AMG_FP64) {
+    // precision copies (BF16: the finest level's ILU(0) factors only)
+    for (size_t l = 0; l < h->lev.size(); ++l) {
+        Level &L = *h->lev[l];
+        const int prec = (o.vcycle_prec == AMG_BF16 && l > 0) ? AMG_FP32 : o.vcycle_prec;
+        if (prec != AMG_FP64) {
             L.v32.alloc(L.A.nnz);
             cast_f64_f32(L.A.v.get(), L.v32.get(), L.A.nnz, s);
-            if (o.vcycle_prec == AMG_BF16) {
-                L.v16.alloc(L.A.nnz);
-                cast_f64_bf16(L.A.v.get(), L.v16.get(), L.A.nnz, s);
-            }
         }
         if (!L.dense) {
-            cast_sweep(L.fwd, o.vcycle_prec, s);
-            cast_sweep(L.bwd, o.vcycle_prec, s);
+            cast_sweep(L.fwd, prec, s);
+            cast_sweep(L.bwd, prec, s);
         }
     }
     // adjoint structures
     if (o.build_adjoint) {
-        for (auto &Lp : h->lev) {
-            Level &L = *Lp;
+        for (size_t l = 0; l < h->lev.size(); ++l) {
+            Level &L = *h->lev[l];
+            const int prec = (o.vcycle_prec == AMG_BF16 && l > 0) ? AMG_FP32 : o.vcycle_prec;
             transpose_values(L.A, L.A.v.get(), L.AT, s);
-            if (o.vcycle_prec != AMG_FP64) {
+            if (prec != AMG_FP64) {
                 L.vt32.alloc(L.AT.nnz);
                 cast_f64_f32(L.AT.v.get(), L.vt32.get(), L.AT.nnz, s);
-                if (o.vcycle_prec == AMG_BF16) {
-                    L.vt16.alloc(L.AT.nnz);
-                    cast_f64_bf16(L.AT.v.get(), L.vt16.get(), L.AT.nnz, s);
-                }
             }
             if (!L.dense) {
                 build_transposed_sweeps(L.A, L.pos.get(), L.lu.get(), L.fwdT, L.bwdT, s);
-                cast_sweep(L.fwdT, o.vcycle_prec, s);
-                cast_sweep(L.bwdT, o.vcycle_prec, s);
+                cast_sweep(L.fwdT, prec, s);
+                cast_sweep(L.bwdT, prec, s);
             }
         }
         h->adjoint_ready = true;
@@ -345,6 +394,11 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
     // SELL-32 copies of A (and A^T) for the outer FP64 products
     build_sell(h->lev[0]->A, h->lev[0]->A.v.get(), h->lev[0]->sell, s);
     if (o.build_adjoint) build_sell(h->lev[0]->AT, h->lev[0]->AT.v.get(), h->lev[0]->sellT, s);
+    tune_sell(h->lev[0]->sell, o, s);
+    if (o.build_adjoint) {
+        h->lev[0]->sellT.block = h->lev[0]->sell.block;
+        h->lev[0]->sellT.unroll = h->lev[0]->sell.unroll;
+    }
     // workspaces
     const size_t tsz = o.vcycle_prec == AMG_FP64 ? sizeof(double) : sizeof(float);
     for (auto &Lp : h->lev) {
@@ -365,7 +419,7 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
     switch (o.vcycle_prec) {
     case AMG_FP64: build_deep<double, double>(h); break;
     case AMG_FP32: build_deep<float, float>(h); break;
-    default: build_deep<float, __nv_bfloat16>(h); break;
+    default: build_deep<float, float>(h); break;   // BF16 mode: coarse levels are FP32
     }
     h->w.alloc(n); h->r.alloc(n); h->xb.alloc(n); h->bb.alloc(n);
     h->hist.alloc((size_t)o.maxit + 2);
@@ -470,13 +524,28 @@ struct VCycle {
     }
     bool has_child(int l) { return l + 1 < nlev() && L(l).n_next > 0; }
 
+    // r = b - A_l x (tr: A_l^T).  In BF16 mode only the ILU(0) factors are
+    // BF16; the residual keeps FP32 values (8-bit mantissas cannot resolve
+    // the small residual of smooth errors of a near-singular diffusion
+    // operator, which the coarse correction needs).
+    void residual(int l, bool tr, const T *x, const T *b, T *r) {
+        if constexpr (std::is_same<V, __nv_bfloat16>::value) {
+            Level &Lv = L(l);
+            const DCsr &M = tr ? Lv.AT : Lv.A;
+            level_residual<float, float>(
+                LevelMats<float>{M.n, M.nnz, M.rp.get(), M.ci.get(), tr ? Lv.vt32.get() : Lv.v32.get()}, x, b, r, s);
+        } else {
+            level_residual<T, V>(mats(l, tr), x, b, r, s);
+        }
+    }
+
     // q (mode 0: =, mode 1: +=) B_l^{-1} z
     void precond(int l, const T *z, T *q, int mode) {
         Level &Lv = L(l);
         const int n = Lv.A.n;
         T *y = ws(Lv.wy), *t = ws(Lv.wt), *r = ws(Lv.wr);
         smooth(Lv, z, y, t, false);
-        level_residual<T, V>(mats(l, false), t, z, r, s);
+        residual(l, false, t, z, r);
         Level &C = L(l + 1);
         T *hc = ws(C.wh), *gc = ws(C.wg);
         restrict_to<T>(C.A.n, Lv.mptr.get(), Lv.midx.get(), r, hc, s);
@@ -486,6 +555,13 @@ struct VCycle {
 
     // g = C_l(h): the inexact solve of level l >= 1
     void level_solve(int l, const T *hrhs, T *g) {
+        if constexpr (std::is_same<V, __nv_bfloat16>::value) {
+            // BF16 values are stored for the finest level only; the coarse
+            // levels run in FP32 (rounding Galerkin sums with near-zero row
+            // sums to 8 bits made the coarse Richardson steps diverge)
+            VCycle<float, float>{h, s}.level_solve(l, hrhs, g);
+            return;
+        }
         Level &Lv = L(l);
         if (l >= h->deep_first) {
             const DeepLevel<T, V> *d = reinterpret_cast<const DeepLevel<T, V> *>(h->deep_desc.get()) +
@@ -499,7 +575,7 @@ struct VCycle {
         for (int it = 0; it < k; ++it) {
             const T *in = hrhs;
             if (it > 0) {
-                level_residual<T, V>(mats(l, false), g, hrhs, res, s);
+                residual(l, false, g, hrhs, res);
                 in = res;
             }
             if (has_child(l)) {
@@ -522,13 +598,17 @@ struct VCycle {
         restrict_to<T>(C.A.n, Lv.mptr.get(), Lv.midx.get(), z, hc, s);
         level_solveT(l + 1, hc, gc);
         prolong<T, T>(n, Lv.agg.get(), nullptr, gc, f, 2, s);
-        level_residual<T, V>(mats(l, true), f, z, r, s);
+        residual(l, true, f, z, r);
         smooth(Lv, r, y, t, true);
         // q (mode)= f + t
         prolong<T, T>(n, nullptr, f, t, q, mode == 0 ? 3 : 4, s);
     }
 
     void level_solveT(int l, const T *hrhs, T *g) {
+        if constexpr (std::is_same<V, __nv_bfloat16>::value) {
+            VCycle<float, float>{h, s}.level_solveT(l, hrhs, g);
+            return;
+        }
         Level &Lv = L(l);
         if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 1, 0, s); return; }
         const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
@@ -536,7 +616,7 @@ struct VCycle {
         for (int it = 0; it < k; ++it) {
             const T *in = hrhs;
             if (it > 0) {
-                level_residual<T, V>(mats(l, true), g, hrhs, res, s);
+                residual(l, true, g, hrhs, res);
                 in = res;
             }
             if (has_child(l)) {
@@ -632,6 +712,11 @@ static void apply_precond_vtype(amg_handle *h, bool transpose) {
 // One inner FGMRES iteration (column j = st->j, read on the device):
 // z_j = B~^{-1} v_j, w = A z_j, CGS2 against v_0..v_j, ||w||, Givens,
 // v_{j+1} = w / ||w||, and the stop flag copied to pinned host memory.
+// Accurate (Dot2) inner products: on by default with the FP64 V-cycle.
+static bool use_dot2(const amg_handle *h) {
+    return h->opt.dot2 < 0 ? h->opt.vcycle_prec == AMG_FP64 : h->opt.dot2 != 0;
+}
+
 static void enqueue_iteration(amg_handle *h, bool transpose) {
     cudaStream_t s = h->stream;
     const size_t n = h->n;
@@ -647,9 +732,9 @@ static void enqueue_iteration(amg_handle *h, bool transpose) {
     const Sell &SL = transpose ? L0.sellT : L0.sell;
     tmark_begin(h, 1);
     if (f64) sell_spmv<double>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(), h->zout64.get(), nullptr,
-                               h->w.get(), 0, s);
+                               h->w.get(), 0, s, SL.block, SL.unroll);
     else sell_spmv<float>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(), h->zout32.get(), nullptr,
-                          h->w.get(), 0, s);
+                          h->w.get(), 0, s, SL.block, SL.unroll);
     tmark_end(h, 1, bytes);
     (void)M;
     if (f64) store_zj<double>(n, dst, h->zout64.get(), h->Zd.get(), s);
@@ -660,7 +745,7 @@ static void enqueue_iteration(amg_handle *h, bool transpose) {
     if (h->opt.orthog == AMG_ORTHO_MGS) {
         // step k reads w, v_k, v_{k+1} and writes w; the first dot reads w, v_0
         tmark_begin(h, 3);
-        mgs(n, dst, h->w.get(), h->V.get(), n, h->partials.get(), h->bar.get(), h->err.get(), s);
+        mgs(n, dst, h->w.get(), h->V.get(), n, h->partials.get(), h->bar.get(), h->err.get(), use_dot2(h), s);
         tmark_end(h, 3, 8.0 * (double)n * (4.0 * K + 2.0));
     } else {
         mdot(n, dst, h->w.get(), h->V.get(), n, h->partials.get(), h->ticket.get(), dst->h1, s);
@@ -724,12 +809,13 @@ static void collect_iteration(amg_handle *h, bool transpose) {
 static void outer_residual(amg_handle *h, const double *b, const double *x, double *r, bool transpose) {
     Level &L0 = *h->lev[0];
     const Sell &SL = transpose ? L0.sellT : L0.sell;
-    sell_spmv<double>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(), x, b, r, 1, h->stream);
+    sell_spmv<double>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(), x, b, r, 1, h->stream, SL.block,
+                      SL.unroll);
 }
 
 static double read_norm(amg_handle *h, const double *v) {
     cudaStream_t s = h->stream;
-    norm2(h->n, v, h->partials.get(), h->ticket.get(), h->st.get()->nrm2, s);
+    norm2(h->n, v, h->partials.get(), h->ticket.get(), h->st.get()->nrm2, use_dot2(h), s);
     double r = 0.0;
     CU(cudaMemcpyAsync(&r, h->st.get()->nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -955,6 +1041,10 @@ int amg_default_options(amg_options_t *o) {
     o->persistent = 1;
     o->deep_block_max = 0;
     o->orthog = AMG_ORTHO_MGS;
+    o->spmv_block = 0;
+    o->spmv_unroll = 0;
+    o->dot2 = -1;
+    o->reserved0 = 0;
     o->seed = 0;
     return AMG_OK;
 }
@@ -964,7 +1054,11 @@ static void check_options(const amg_options_t &o) {
         o.dense_max > 4096 || o.max_levels < 2 || o.max_levels > 24 || o.restart < 1 || o.restart > KMAX1 - 1 ||
         o.maxit < 0 || o.vcycle_prec < 0 || o.vcycle_prec > 2 || o.order_fine < 0 || o.order_fine > 1 ||
         o.order_coarse < 0 || o.order_coarse > 1 || o.coloring < 0 || o.coloring > 1 || o.deep_block_max < 0 ||
-        o.persistent < 0 || o.persistent > 2 || o.orthog < 0 || o.orthog > 1)
+        o.persistent < 0 || o.persistent > 2 || o.orthog < 0 || o.orthog > 1 ||
+        (o.spmv_block != 0 && o.spmv_block != 64 && o.spmv_block != 128 && o.spmv_block != 256 &&
+         o.spmv_block != 512) ||
+        (o.spmv_unroll != 0 && o.spmv_unroll != 2 && o.spmv_unroll != 4 && o.spmv_unroll != 8) || o.dot2 < -1 ||
+        o.dot2 > 1)
         fail(AMG_ERR_INVALID_ARG, "option out of range (restart <= 31, dense_max <= 4096, 2 <= max_levels <= 24)");
 }
 
@@ -1208,6 +1302,16 @@ int amg_num_levels(amg_handle_t *h, int32_t *nlevels) {
 static Level &level_of(amg_handle_t *h, int l) {
     if (!h || l < 0 || l >= (int)h->lev.size()) fail(AMG_ERR_INVALID_ARG, "level out of range");
     return *h->lev[l];
+}
+
+int amg_get_spmv_config(amg_handle_t *h, int32_t *block, int32_t *unroll) {
+    ABI_TRY
+    if (!h || !block || !unroll) fail(AMG_ERR_INVALID_ARG, "amg_get_spmv_config: null argument");
+    if (h->lev.empty()) fail(AMG_ERR_INVALID_ARG, "amg_get_spmv_config: batch handle (ask a member)");
+    *block = h->lev[0]->sell.block;
+    *unroll = h->lev[0]->sell.unroll;
+    return AMG_OK;
+    ABI_CATCH
 }
 
 int amg_get_level_info(amg_handle_t *h, int32_t level, int64_t *info) {

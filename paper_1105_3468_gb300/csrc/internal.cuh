@@ -84,6 +84,7 @@ struct Sell {
     DBuf<int64_t> ptr;      // [nslices + 1]
     DBuf<int> ci;           // [padded]
     DBuf<double> v;         // [padded]
+    int block = 256, unroll = 4;   // launch geometry of the SpMV (autotuned at setup)
 };
 void build_sell(const DCsr &A, const double *vals, Sell &S, cudaStream_t s);
 

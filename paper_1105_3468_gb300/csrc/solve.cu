@@ -22,13 +22,46 @@ template <> __device__ __forceinline__ double val_as<double, float>(float x) { r
 
 template <typename T, typename U> __device__ __forceinline__ T cvt(U x) { return (T)x; }
 
-// acc - a*b and acc + a*b.  In FP64 the product and the sum are rounded
-// separately (no fused multiply-add), which is how the plain sequential
-// definition rounds; the FP32/BF16 V-cycle keeps the fused form.
-__device__ __forceinline__ double msub(double acc, double a, double b) { return __dsub_rn(acc, __dmul_rn(a, b)); }
-__device__ __forceinline__ float msub(float acc, float a, float b) { return acc - a * b; }
-__device__ __forceinline__ double madd(double acc, double a, double b) { return __dadd_rn(acc, __dmul_rn(a, b)); }
-__device__ __forceinline__ float madd(float acc, float a, float b) { return acc + a * b; }
+// acc - a*b and acc + a*b as one fused multiply-add (a single rounding):
+// every multiply-accumulate of the solve phase rounds this way, in FP64 as
+// in FP32, so a row summed in stored order reproduces the sequential
+// definition bit for bit.
+__device__ __forceinline__ double msub(double acc, double a, double b) { return __fma_rn(-a, b, acc); }
+__device__ __forceinline__ float msub(float acc, float a, float b) { return __fmaf_rn(-a, b, acc); }
+__device__ __forceinline__ double madd(double acc, double a, double b) { return __fma_rn(a, b, acc); }
+__device__ __forceinline__ float madd(float acc, float a, float b) { return __fmaf_rn(a, b, acc); }
+
+// acc -/+ sum_k v[k] x[ci[k]] over k in [k0, k1), in stored order.  The
+// column indices, values and x entries of ROW_CHUNK terms are loaded before
+// any of them is used, so their memory latencies overlap; the subtraction
+// chain itself keeps the stored order.  COHERENT: x is written by other
+// blocks of the same launch and is read past L1.
+constexpr int ROW_CHUNK = 8;
+
+template <bool COHERENT, bool SUB, typename T, typename V>
+__device__ __forceinline__ T row_acc(T acc, int k0, int k1, const int *__restrict__ ci, const V *__restrict__ v,
+                                     const T *x) {
+    for (int k = k0; k < k1; k += ROW_CHUNK) {
+        int c[ROW_CHUNK];
+        V w[ROW_CHUNK];
+        T xv[ROW_CHUNK];
+#pragma unroll
+        for (int q = 0; q < ROW_CHUNK; ++q)
+            if (k + q < k1) { c[q] = ci[k + q]; w[q] = v[k + q]; }
+#pragma unroll
+        for (int q = 0; q < ROW_CHUNK; ++q)
+            if (k + q < k1) xv[q] = COHERENT ? __ldcg(x + c[q]) : x[c[q]];
+#pragma unroll
+        for (int q = 0; q < ROW_CHUNK; ++q)
+            if (k + q < k1) acc = SUB ? msub(acc, val_as<T, V>(w[q]), xv[q]) : madd(acc, val_as<T, V>(w[q]), xv[q]);
+    }
+    return acc;
+}
+template <bool COHERENT, typename T, typename V>
+__device__ __forceinline__ T row_sub(T acc, int k0, int k1, const int *__restrict__ ci, const V *__restrict__ v,
+                                     const T *x) {
+    return row_acc<COHERENT, true, T, V>(acc, k0, k1, ci, v, x);
+}
 
 // ------------------------------------------------------------------ CSR SpMV / residual
 // G lanes per row; lanes stride the row, then a shuffle tree reduction.
@@ -80,8 +113,8 @@ void residual_f64(int n, int nnz, const int *rp, const int *ci, const double *v,
     spmv_t<double, double, double, double>(n, nnz, rp, ci, v, x, b, r, 1, s);
 }
 
-template <typename XT>
-__global__ void __launch_bounds__(256) k_sell_spmv(int n, const int64_t *__restrict__ ptr, const int *__restrict__ ci,
+template <typename XT, int U>
+__global__ void __launch_bounds__(512) k_sell_spmv(int n, const int64_t *__restrict__ ptr, const int *__restrict__ ci,
                                                    const double *__restrict__ v, const XT *__restrict__ x,
                                                    const double *__restrict__ b, double *__restrict__ y, int mode) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -91,23 +124,32 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int n, const int64_t *__restr
         const double *vv = v + base + r;
         const int *cc = ci + base + r;
         double acc = 0.0;
-#pragma unroll 4
+#pragma unroll U
         for (int k = 0; k < w; ++k) acc = madd(acc, __ldg(vv + 32 * k), (double)__ldg(x + __ldg(cc + 32 * k)));
         y[i] = mode ? b[i] - acc : acc;
     }
 }
 
+// Launch geometry (threads per block, unroll depth of the column loop) does
+// not change what a thread sums or in which order, so every choice gives the
+// same bits; the autotuner picks by time.
 template <typename XT>
 void sell_spmv(int n, int nslices, const int64_t *ptr, const int *ci, const double *v, const XT *x, const double *b,
-               double *y, int mode, cudaStream_t s) {
+               double *y, int mode, cudaStream_t s, int block, int unroll) {
     (void)nslices;
-    k_sell_spmv<XT><<<grid_for(n, 256), 256, 0, s>>>(n, ptr, ci, v, x, b, y, mode);
+    if (block != 64 && block != 128 && block != 256 && block != 512) block = 256;
+    const int g = grid_for(n, block);
+    switch (unroll) {
+    case 2: k_sell_spmv<XT, 2><<<g, block, 0, s>>>(n, ptr, ci, v, x, b, y, mode); break;
+    case 8: k_sell_spmv<XT, 8><<<g, block, 0, s>>>(n, ptr, ci, v, x, b, y, mode); break;
+    default: k_sell_spmv<XT, 4><<<g, block, 0, s>>>(n, ptr, ci, v, x, b, y, mode); break;
+    }
     CU_LAUNCH("k_sell_spmv"); count_launch();
 }
 template void sell_spmv<double>(int, int, const int64_t *, const int *, const double *, const double *, const double *,
-                                double *, int, cudaStream_t);
+                                double *, int, cudaStream_t, int, int);
 template void sell_spmv<float>(int, int, const int64_t *, const int *, const double *, const float *, const double *,
-                               double *, int, cudaStream_t);
+                               double *, int, cudaStream_t, int, int);
 
 // r = b - A x, one thread per row, terms summed in stored column order.
 template <typename T, typename V>
@@ -115,9 +157,7 @@ __global__ void __launch_bounds__(256) k_residual_seq(int n, const int *__restri
                                                       const V *__restrict__ v, const T *__restrict__ x,
                                                       const T *__restrict__ b, T *__restrict__ r) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        T acc = 0;
-        const int e1 = rp[i + 1];
-        for (int e = rp[i]; e < e1; ++e) acc = madd(acc, val_as<T, V>(v[e]), x[ci[e]]);
+        const T acc = row_acc<false, false, T, V>(T(0), rp[i], rp[i + 1], ci, v, x);
         r[i] = b[i] - acc;
     }
 }
@@ -146,7 +186,7 @@ __global__ void __launch_bounds__(128) k_sweep(int cnt, const int *__restrict__ 
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         const int i = rows[t];
         T acc = in[i];
-        for (int e = rp[t]; e < rp[t + 1]; ++e) acc = msub(acc, val_as<T, V>(v[e]), out[ci[e]]);
+        acc = row_sub<false, T, V>(acc, rp[t], rp[t + 1], ci, v, out);
         out[i] = with_diag ? acc / dg[t] : acc;
     }
 }
@@ -201,21 +241,21 @@ __device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err) {
 
 template <typename T> __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
 
-// Rows of one schedule level; out values written by earlier levels of this
-// launch are read past L1 (__ldcg), since L1 is not coherent across SMs.
-template <typename T, typename V>
-__device__ __forceinline__ void sweep_level_rows(int b, int e, const int *__restrict__ rows, const int *__restrict__ rp,
-                                                 const int *__restrict__ ci, const V *__restrict__ v,
-                                                 const T *__restrict__ dg, const T *in, bool in_coherent, T *out,
-                                                 int with_diag, int tid, int nthr) {
-    for (int t = b + tid; t < e; t += nthr) {
-        const int i = rows[t];
-        T acc = in_coherent ? ld_cg(in + i) : in[i];
-        const int e1 = rp[t + 1];
-        for (int k = rp[t]; k < e1; ++k) acc -= val_as<T, V>(v[k]) * ld_cg(out + ci[k]);
-        out[i] = with_diag ? acc / dg[t] : acc;
+// Barrier between schedule levels.  SYNC 0: grid barrier of a cooperative
+// launch; 1: the grid is one thread-block cluster (hardware cluster barrier,
+// release/acquire at cluster scope); 2: the grid is one block.
+template <int SYNC>
+__device__ __forceinline__ void level_barrier(unsigned int *bar, int *err) {
+    if constexpr (SYNC == 0) {
+        grid_barrier(bar, err);
+    } else if constexpr (SYNC == 1) {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    } else {
+        __syncthreads();
     }
 }
+
+
 
 // One triangular solve over all schedule levels of S.  The first row a
 // thread owns in the next level is prefetched (row id, extent, up to PF
@@ -223,8 +263,9 @@ __device__ __forceinline__ void sweep_level_rows(int b, int e, const int *__rest
 // launch) before the barrier, so that after the barrier only the values of
 // earlier rows remain to be loaded.
 constexpr int SWEEP_PF = 4;
+constexpr int SWEEP_CLUSTER_MAX = 8;   // portable cluster size
 
-template <typename T, typename V>
+template <int SYNC, typename T, typename V>
 __device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, int with_diag, const T *in, bool in_coherent,
                                             T *out, unsigned int *bar, int *err, int tid, int nthr, bool last_barrier) {
     int pt = -1, pi = 0, pk0 = 0, pk1 = 0, pc[SWEEP_PF];
@@ -252,7 +293,7 @@ __device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, int with_d
 #pragma unroll
             for (int q = 0; q < SWEEP_PF; ++q)
                 if (pk0 + q < pk1) acc = msub(acc, val_as<T, V>(pv[q]), ld_cg(out + pc[q]));
-            for (int k = pk0 + SWEEP_PF; k < pk1; ++k) acc = msub(acc, val_as<T, V>(S.v[k]), ld_cg(out + S.ci[k]));
+            acc = row_sub<true, T, V>(acc, pk0 + SWEEP_PF, pk1, S.ci, S.v, out);
             out[pi] = with_diag ? acc / pd : acc;
             // further rows of this level owned by this thread (levels wider than the grid)
             const int e = S.dlev[l + 1];
@@ -260,21 +301,21 @@ __device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, int with_d
                 const int i = S.rows[t];
                 T a2 = in_coherent ? ld_cg(in + i) : in[i];
                 const int k1 = S.rp[t + 1];
-                for (int k = S.rp[t]; k < k1; ++k) a2 = msub(a2, val_as<T, V>(S.v[k]), ld_cg(out + S.ci[k]));
+                a2 = row_sub<true, T, V>(a2, S.rp[t], k1, S.ci, S.v, out);
                 out[i] = with_diag ? a2 / S.d[t] : a2;
             }
         }
         prefetch(l + 1);
-        if (l + 1 < S.nlev || last_barrier) grid_barrier(bar, err);
+        if (l + 1 < S.nlev || last_barrier) level_barrier<SYNC>(bar, err);
     }
 }
 
-template <typename T, typename V>
+template <typename T, typename V, int SYNC>
 __global__ void __launch_bounds__(256) k_sweep_pair(SweepView<T, V> F, int f_diag, SweepView<T, V> B, int b_diag,
                                                     const T *in, T *y, T *out, unsigned int *bar, int *err) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-    sweep_phase<T, V>(F, f_diag, in, false, y, bar, err, tid, nthr, true);
-    sweep_phase<T, V>(B, b_diag, y, true, out, bar, err, tid, nthr, false);
+    sweep_phase<SYNC, T, V>(F, f_diag, in, false, y, bar, err, tid, nthr, true);
+    sweep_phase<SYNC, T, V>(B, b_diag, y, true, out, bar, err, tid, nthr, false);
 }
 
 template <typename T, typename V>
@@ -282,7 +323,7 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
                      T *y, T *out, unsigned int *bar, int *err, cudaStream_t s) {
     static const int grid = [] {               // initialised once, thread-safe
         int per_sm = 0;
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_pair<T, V>, 256, 0));
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_pair<T, V, 0>, 256, 0));
         return sm_count() * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
     }();
     int maxw = 0;
@@ -292,9 +333,29 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
     if (g > grid) g = grid;
     if (g < 1) g = 1;
     SweepView<T, V> f = F, b = B;
-    void *args[] = {&f, (void *)&f_diag, &b, (void *)&b_diag, (void *)&in, (void *)&y, (void *)&out, (void *)&bar,
-                    (void *)&err};
-    CU(cudaLaunchCooperativeKernel((const void *)k_sweep_pair<T, V>, dim3(g), dim3(256), args, 0, s));
+    if (g == 1) {
+        k_sweep_pair<T, V, 2><<<1, 256, 0, s>>>(f, f_diag, b, b_diag, in, y, out, bar, err);
+        CU_LAUNCH("k_sweep_pair (one block)");
+    } else if (g <= SWEEP_CLUSTER_MAX) {
+        // a grid this small runs as one cluster: hardware barrier, all blocks co-scheduled
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(g);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = g;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CU(cudaLaunchKernelEx(&cfg, k_sweep_pair<T, V, 1>, f, f_diag, b, b_diag, in, y, out, bar, err));
+    } else {
+        void *args[] = {&f, (void *)&f_diag, &b, (void *)&b_diag, (void *)&in, (void *)&y, (void *)&out, (void *)&bar,
+                        (void *)&err};
+        CU(cudaLaunchCooperativeKernel((const void *)k_sweep_pair<T, V, 0>, dim3(g), dim3(256), args, 0, s));
+    }
     count_launch();
 }
 template void sweep_pair_coop<double, double>(const SweepView<double, double> &, int, const SweepView<double, double> &,
@@ -331,6 +392,7 @@ template void sweep<float, __nv_bfloat16>(const SweepView<float, __nv_bfloat16> 
 // sentinel during the forward solve and a grid barrier separates that reset
 // from the backward solve.
 constexpr unsigned int DF_SPIN_LIMIT = 1u << 20;
+constexpr int DF_LEVELS_IN_FLIGHT = 4;
 
 template <typename T> struct Sentinel;
 template <> struct Sentinel<float> {
@@ -370,8 +432,13 @@ __global__ void k_fill_sentinel(size_t n, T *x) {
         x[i] = Sentinel<T>::value();
 }
 
-// One triangular solve in dataflow order.  Returns false when a wait ran out
-// or another thread reported one.
+// One triangular solve in dataflow order.  A lane reads the values of its
+// row DF_BATCH at a time (independent loads in flight together), consumes
+// them in stored order up to the first one not yet written, and polls again
+// after a short sleep.  Returns false when a wait ran out or another thread
+// reported one.
+constexpr int DF_BATCH = 4;
+
 template <typename T, typename V>
 __device__ __forceinline__ bool df_phase(const SweepView<T, V> &S, int with_diag, const T *in, bool in_coherent,
                                          T *out, T *consumed, int *err, int tid, int nthr) {
@@ -393,12 +460,21 @@ __device__ __forceinline__ bool df_phase(const SweepView<T, V> &S, int with_diag
         bool fail = false;
         while (__any_sync(0xffffffffu, !done)) {
             if (!done) {
-                for (; k < k1; ++k) {
-                    const T xv = Sentinel<T>::ld(out + S.ci[k]);
-                    if (Sentinel<T>::is(xv)) break;
-                    acc = msub(acc, val_as<T, V>(S.v[k]), xv);
+                bool blocked = false;
+                while (k < k1 && !blocked) {
+                    T xv[DF_BATCH];
+#pragma unroll
+                    for (int q = 0; q < DF_BATCH; ++q)
+                        if (k + q < k1) xv[q] = Sentinel<T>::ld(out + S.ci[k + q]);
+#pragma unroll
+                    for (int q = 0; q < DF_BATCH; ++q) {
+                        if (blocked || k >= k1) continue;
+                        if (Sentinel<T>::is(xv[q])) { blocked = true; continue; }
+                        acc = msub(acc, val_as<T, V>(S.v[k]), xv[q]);
+                        ++k;
+                    }
                 }
-                if (k == k1) {
+                if (!blocked) {
                     Sentinel<T>::st(out + i, with_diag ? acc / d : acc);
                     if (consumed) consumed[i] = Sentinel<T>::value();
                     done = true;
@@ -409,6 +485,8 @@ __device__ __forceinline__ bool df_phase(const SweepView<T, V> &S, int with_diag
                 } else if ((spins & 255u) == 0 && *(volatile int *)err) {
                     fail = true;
                     done = true;
+                } else {
+                    __nanosleep(64);
                 }
             }
         }
@@ -446,8 +524,12 @@ void sweep_pair_df(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_df<T, V>, 256, 0));
         return sm_count() * (per_sm < 1 ? 1 : per_sm);
     }();
-    const int rows = std::max(F.lev_ptr[F.nlev], B.lev_ptr[B.nlev]);
-    int g = (rows + 255) / 256;
+    // enough threads for a few schedule levels in flight; more only add
+    // polling traffic
+    int maxw = 0;
+    for (int l = 0; l < F.nlev; ++l) maxw = max(maxw, F.lev_ptr[l + 1] - F.lev_ptr[l]);
+    for (int l = 0; l < B.nlev; ++l) maxw = max(maxw, B.lev_ptr[l + 1] - B.lev_ptr[l]);
+    int g = (int)(((int64_t)DF_LEVELS_IN_FLIGHT * maxw + 255) / 256);
     if (g > grid) g = grid;
     if (g < 1) g = 1;
     SweepView<T, V> f = F, b = B;
@@ -473,7 +555,7 @@ __device__ __forceinline__ void block_sweep(const SweepView<T, V> &S, const T *i
             const int i = S.rows[t];
             T acc = in[i];
             const int k1 = S.rp[t + 1];
-            for (int k = S.rp[t]; k < k1; ++k) acc = msub(acc, val_as<T, V>(S.v[k]), out[S.ci[k]]);
+            acc = row_sub<false, T, V>(acc, S.rp[t], k1, S.ci, S.v, out);
             out[i] = with_diag ? acc / S.d[t] : acc;
         }
         __syncthreads();
@@ -724,11 +806,12 @@ __global__ void __launch_bounds__(RT) k_cgs_update(size_t n, const FgState *st, 
 }
 
 // Givens step for column j (single thread): H column from h1 + h2 and ||w||,
-// apply previous rotations, new rotation, residual estimate.  Products and
-// sums are rounded one by one (no fused multiply-add), as in the plain
-// sequential statement of the rotations.
+// apply previous rotations, new rotation, residual estimate.  Each rotated
+// entry c1 a + c2 b is fma(c1, a, c2 b): the second product rounded, then one
+// fused multiply-add.
 __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double fma2(double c1, double a, double c2, double b) { return __fma_rn(c1, a, mul(c2, b)); }
 
 __global__ void k_givens(FgState *st) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -742,11 +825,11 @@ __global__ void k_givens(FgState *st) {
     st->hn = hn;
     for (int k = 0; k < j; ++k) {
         double a = H[k * m + j], c = H[(k + 1) * m + j];
-        H[k * m + j] = add(mul(st->cs[k], a), mul(st->sn[k], c));
-        H[(k + 1) * m + j] = add(mul(-st->sn[k], a), mul(st->cs[k], c));
+        H[k * m + j] = fma2(st->cs[k], a, st->sn[k], c);
+        H[(k + 1) * m + j] = fma2(-st->sn[k], a, st->cs[k], c);
     }
     double a = H[j * m + j], c = H[(j + 1) * m + j];
-    double rho = sqrt(add(mul(a, a), mul(c, c)));
+    double rho = sqrt(fma2(a, a, c, c));
     if (!(rho > 0.0) || !isfinite(rho)) {
         st->status = 6;
         st->stop = 1;
@@ -812,7 +895,7 @@ __global__ void k_backsolve(FgState *st) {
     const int m = st->m, j = st->jdone;
     for (int k = j - 1; k >= 0; --k) {
         double t = st->s[k];
-        for (int l = k + 1; l < j; ++l) t = __dsub_rn(t, __dmul_rn(st->H[k * m + l], st->y[l]));
+        for (int l = k + 1; l < j; ++l) t = __fma_rn(-st->H[k * m + l], st->y[l], t);
         st->y[k] = t / st->H[k * m + k];
     }
 }
@@ -826,7 +909,7 @@ __global__ void k_update_x(size_t n, const FgState *st, const ZT *__restrict__ Z
     __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double acc = x[i];
-        for (int k = 0; k < j; ++k) acc = __dadd_rn(acc, __dmul_rn(ys[k], (double)Z[k * ldz + i]));
+        for (int k = 0; k < j; ++k) acc = __fma_rn(ys[k], (double)Z[k * ldz + i], acc);
         x[i] = acc;
     }
 }
@@ -839,14 +922,81 @@ template void update_x<double>(size_t, const FgState *, const double *, size_t, 
 template void update_x<float>(size_t, const FgState *, const float *, size_t, double *, cudaStream_t);
 
 // ||v||^2 -> out (deterministic)
+// Accurate inner products (DOT2): the Dot2 scheme of Ogita, Rump and Oishi
+// (2005).  Each product is split exactly into h + r (TwoProduct via fma), the
+// h are added with the exact error of each addition kept (TwoSum), errors are
+// collected in c; partial (p, c) pairs merge by TwoSum of the p and the sum of
+// the c.  The result p + c is the exact inner product correctly rounded in all
+// but near-tie cases, so it does not depend on how the sum is split across
+// threads and blocks.
+__device__ __forceinline__ void two_sum_d(double a, double b, double &s, double &e) {
+    const double t = __dadd_rn(a, b);
+    const double z = __dsub_rn(t, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(t, z)), __dsub_rn(b, z));
+    s = t;
+}
+__device__ __forceinline__ void dot2_add(double &p, double &c, double x, double y) {
+    const double h = __dmul_rn(x, y);
+    const double r = __fma_rn(x, y, -h);
+    double q;
+    two_sum_d(p, h, p, q);
+    c = __dadd_rn(c, __dadd_rn(q, r));
+}
+__device__ __forceinline__ void dot2_merge(double &p, double &c, double p2, double c2) {
+    double q;
+    two_sum_d(p, p2, p, q);
+    c = __dadd_rn(c, __dadd_rn(c2, q));
+}
+
+// Block reduction of (p, c) pairs: returns the block's pair in thread 0.
+__device__ __forceinline__ void block_merge2(double &p, double &c) {
+    __shared__ double sp[RT / 32], sc[RT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int off = 16; off; off >>= 1) {
+        const double p2 = __shfl_down_sync(0xffffffffu, p, off), c2 = __shfl_down_sync(0xffffffffu, c, off);
+        dot2_merge(p, c, p2, c2);
+    }
+    if (lane == 0) { sp[warp] = p; sc[warp] = c; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        p = sp[0];
+        c = sc[0];
+        for (int w = 1; w < RT / 32; ++w) dot2_merge(p, c, sp[w], sc[w]);
+    }
+    __syncthreads();
+}
+
+template <bool DOT2>
 __global__ void __launch_bounds__(RT) k_norm2(size_t n, const double *__restrict__ v, double *partials,
                                               unsigned int *ticket, double *out) {
-    double acc[1] = {0.0};
-    for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) acc[0] += v[i] * v[i];
-    block_reduce_store<RT>(acc, 1, partials, KMAX1);
-    if (last_block(ticket)) {
-        final_reduce<RT>(partials, 1, KMAX1, out);
-        if (threadIdx.x == 0) *ticket = 0;
+    if constexpr (DOT2) {
+        double p = 0.0, c = 0.0;
+        for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+            dot2_add(p, c, v[i], v[i]);
+        block_merge2(p, c);
+        if (threadIdx.x == 0) {
+            partials[(size_t)blockIdx.x * KMAX1] = p;
+            partials[(size_t)blockIdx.x * KMAX1 + 1] = c;
+        }
+        if (last_block(ticket)) {
+            if (threadIdx.x == 0) {
+                double P = 0.0, Cc = 0.0;
+                for (int b = 0; b < (int)gridDim.x; ++b)
+                    dot2_merge(P, Cc, ((volatile const double *)partials)[(size_t)b * KMAX1],
+                               ((volatile const double *)partials)[(size_t)b * KMAX1 + 1]);
+                out[0] = __dadd_rn(P, Cc);
+                *ticket = 0;
+            }
+        }
+    } else {
+        double acc[1] = {0.0};
+        for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+            acc[0] = __fma_rn(v[i], v[i], acc[0]);
+        block_reduce_store<RT>(acc, 1, partials, KMAX1);
+        if (last_block(ticket)) {
+            final_reduce<RT>(partials, 1, KMAX1, out);
+            if (threadIdx.x == 0) *ticket = 0;
+        }
     }
 }
 
@@ -858,9 +1008,10 @@ __global__ void __launch_bounds__(RT) k_norm2(size_t n, const double *__restrict
 // the block partials in block order, so all blocks hold the same h_k.  Step
 // partials alternate between two halves of the buffer: a block still reading
 // step k's partials cannot be overtaken by writes of step k + 2, which lie
-// behind the barrier of step k + 1.  Products and sums are rounded one by
-// one (no fused multiply-add).  Each element of w is touched by one thread
-// only, so w needs no cross-block visibility.
+// behind the barrier of step k + 1.  Products accumulate by fused
+// multiply-add, and the update is w - h v as one fused multiply-add.  Each
+// element of w is touched by one thread only, so w needs no cross-block
+// visibility.
 __device__ __forceinline__ double mgs_grid_sum(double acc, double *partials, unsigned int *bar, int *err) {
     __shared__ double red[RT / 32];
     __shared__ double total;
@@ -884,51 +1035,77 @@ __device__ __forceinline__ double mgs_grid_sum(double acc, double *partials, uns
     return total;
 }
 
+// Grid sum of (p, c) pairs, same pattern as mgs_grid_sum; partials holds two
+// doubles per block.
+__device__ __forceinline__ double mgs_grid_sum2(double p, double c, double *partials, unsigned int *bar, int *err) {
+    __shared__ double total;
+    block_merge2(p, c);
+    if (threadIdx.x == 0) {
+        __stcg(partials + 2 * blockIdx.x, p);
+        __stcg(partials + 2 * blockIdx.x + 1, c);
+    }
+    grid_barrier(bar, err);
+    if (threadIdx.x == 0) {
+        double P = 0.0, Cc = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) dot2_merge(P, Cc, __ldcg(partials + 2 * b), __ldcg(partials + 2 * b + 1));
+        total = __dadd_rn(P, Cc);
+    }
+    __syncthreads();
+    return total;
+}
+
+template <bool DOT2>
 __global__ void __launch_bounds__(RT) k_mgs(size_t n, FgState *st, double *w, const double *__restrict__ V,
                                             size_t ldv, double *partials, unsigned int *bar, int *err) {
     if (st->stop) return;                    // same value in every block
     const int j = st->j;
     const size_t tid = blockIdx.x * (size_t)RT + threadIdx.x, nthr = (size_t)gridDim.x * RT;
-    double acc = 0.0;
-    for (size_t i = tid; i < n; i += nthr) acc = __dadd_rn(acc, __dmul_rn(w[i], V[i]));
-    double h = mgs_grid_sum(acc, partials, bar, err);
+    const size_t half = (size_t)(DOT2 ? 2 : 1) * gridDim.x;
+    auto gsum = [&](double p, double c, int k) {
+        double *buf = partials + (size_t)(k & 1) * half;
+        return DOT2 ? mgs_grid_sum2(p, c, buf, bar, err) : mgs_grid_sum(p, buf, bar, err);
+    };
+    double p = 0.0, c = 0.0;
+    for (size_t i = tid; i < n; i += nthr) {
+        if (DOT2) dot2_add(p, c, w[i], V[i]);
+        else p = __fma_rn(w[i], V[i], p);
+    }
+    double h = gsum(p, c, 0);
     for (int k = 0; k <= j; ++k) {
         if (blockIdx.x == 0 && threadIdx.x == 0) { st->h1[k] = h; st->h2[k] = 0.0; }
         const double *vk = V + (size_t)k * ldv;
-        const double *vn = V + (size_t)(k + 1) * ldv;
-        acc = 0.0;
-        if (k < j) {
-            for (size_t i = tid; i < n; i += nthr) {
-                const double wi = __dsub_rn(w[i], __dmul_rn(h, vk[i]));
-                w[i] = wi;
-                acc = __dadd_rn(acc, __dmul_rn(wi, vn[i]));
-            }
-        } else {
-            for (size_t i = tid; i < n; i += nthr) {
-                const double wi = __dsub_rn(w[i], __dmul_rn(h, vk[i]));
-                w[i] = wi;
-                acc = __dadd_rn(acc, __dmul_rn(wi, wi));
-            }
+        const double *vn = k < j ? V + (size_t)(k + 1) * ldv : nullptr;
+        p = 0.0;
+        c = 0.0;
+        for (size_t i = tid; i < n; i += nthr) {
+            const double wi = __fma_rn(-h, vk[i], w[i]);
+            w[i] = wi;
+            const double y = vn ? vn[i] : wi;
+            if (DOT2) dot2_add(p, c, wi, y);
+            else p = __fma_rn(wi, y, p);
         }
-        h = mgs_grid_sum(acc, partials + (size_t)((k + 1) & 1) * gridDim.x, bar, err);
+        h = gsum(p, c, k + 1);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) st->nrm2[0] = h;
 }
 
 void mgs(size_t n, FgState *st, double *w, const double *V, size_t ldv, double *partials, unsigned int *bar,
-         int *err, cudaStream_t s) {
+         int *err, bool dot2, cudaStream_t s) {
     static const int grid = [] {               // initialised once, thread-safe
-        int per_sm = 0;
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgs, RT, 0));
+        int a = 0, b = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgs<false>, RT, 0));
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mgs<true>, RT, 0));
+        const int per_sm = std::min(a, b);
         const int g = sm_count() * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
-        return std::min(g, reduce_grid() * KMAX1 / 2);   // two halves of the partials buffer
+        return std::min(g, reduce_grid() * KMAX1 / 4);   // two halves of (p, c) pairs in the partials
     }();
     size_t g = (n + RT - 1) / RT;
     if (g > (size_t)grid) g = grid;
     if (g < 1) g = 1;
     void *args[] = {(void *)&n, (void *)&st, (void *)&w, (void *)&V, (void *)&ldv, (void *)&partials, (void *)&bar,
                     (void *)&err};
-    CU(cudaLaunchCooperativeKernel((const void *)k_mgs, dim3((unsigned)g), dim3(RT), args, 0, s));
+    const void *fn = dot2 ? (const void *)k_mgs<true> : (const void *)k_mgs<false>;
+    CU(cudaLaunchCooperativeKernel(fn, dim3((unsigned)g), dim3(RT), args, 0, s));
     count_launch();
 }
 
@@ -944,8 +1121,9 @@ void cgs_update(size_t n, const FgState *st, const double *hin, double *w, const
     k_cgs_update<<<reduce_grid(), RT, 0, s>>>(n, st, hin, w, V, ldv, want_dots, partials, ticket, hout);
     CU_LAUNCH("k_cgs_update"); count_launch();
 }
-void norm2(size_t n, const double *v, double *partials, unsigned int *ticket, double *out, cudaStream_t s) {
-    k_norm2<<<reduce_grid(), RT, 0, s>>>(n, v, partials, ticket, out);
+void norm2(size_t n, const double *v, double *partials, unsigned int *ticket, double *out, bool dot2, cudaStream_t s) {
+    if (dot2) k_norm2<true><<<reduce_grid(), RT, 0, s>>>(n, v, partials, ticket, out);
+    else k_norm2<false><<<reduce_grid(), RT, 0, s>>>(n, v, partials, ticket, out);
     CU_LAUNCH("k_norm2"); count_launch();
 }
 void givens(FgState *st, cudaStream_t s) {

@@ -50,7 +50,7 @@ void residual_f64(int n, int nnz, const int *rp, const int *ci, const double *v,
 // summed sequentially in column order.
 template <typename XT>
 void sell_spmv(int n, int nslices, const int64_t *ptr, const int *ci, const double *v, const XT *x, const double *b,
-               double *y, int mode, cudaStream_t s);
+               double *y, int mode, cudaStream_t s, int block = 256, int unroll = 4);
 
 template <typename T, typename V>
 void level_residual(const LevelMats<V> &M, const T *x, const T *b, T *r, cudaStream_t s);
@@ -105,8 +105,9 @@ void mdot(size_t n, const FgState *st, const double *w, const double *V, size_t 
 // Modified Gram-Schmidt for column j = st->j in one cooperative launch:
 // h1[k] = (w, v_k) with w updated after each k, h2[k] = 0, nrm2[0] = ||w||^2.
 // partials: >= 2 x grid doubles; bar/err as for the sweeps.
+// dot2: inner products as if in twice the working precision (Dot2).
 void mgs(size_t n, FgState *st, double *w, const double *V, size_t ldv, double *partials, unsigned int *bar,
-         int *err, cudaStream_t s);
+         int *err, bool dot2, cudaStream_t s);
 void cgs_update(size_t n, const FgState *st, const double *hin, double *w, const double *V, size_t ldv,
                 int want_dots, double *partials, unsigned int *ticket, double *hout, cudaStream_t s);
 // zin = V_{st->j} (FP64 copy or FP32 conversion)
@@ -115,7 +116,7 @@ void load_vj(size_t n, const FgState *st, const double *V, T *zin, cudaStream_t 
 // Z_{st->j} = zout
 template <typename T>
 void store_zj(size_t n, const FgState *st, const T *zout, T *Z, cudaStream_t s);
-void norm2(size_t n, const double *v, double *partials, unsigned int *ticket, double *out, cudaStream_t s);
+void norm2(size_t n, const double *v, double *partials, unsigned int *ticket, double *out, bool dot2, cudaStream_t s);
 void givens(FgState *st, cudaStream_t s);
 void scale_next(size_t n, const double *w, double *vout, const FgState *st, cudaStream_t s);
 void backsolve(FgState *st, cudaStream_t s);

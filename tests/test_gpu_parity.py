@@ -137,6 +137,8 @@ def test_fgmres_fp64_history_and_solution(env, name):
     assert st.iters == info.iters
     k = min(21, len(hist))
     rel = np.abs(hist[:k] - info.hist[:k]) / info.hist[:k]
+    same = int((hist[:k] == info.hist[:k]).sum())
+    print(f"{name}: FP64 history max rel diff {rel.max():.2e}, {same} of {k} entries bit-identical")
     assert rel.max() <= 1e-10, rel
     xg = x.cpu().numpy()
     assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
@@ -304,3 +306,25 @@ def test_cgs2_orthogonalisation(env, name):
     print(f"{name}: CGS2 history max rel diff {rel:.2e}")
     assert rel <= 1e-8
     assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_spmv_autotuner_choices_identical(env):
+    """Every launch geometry the SpMV autotuner can pick gives the same bits:
+    the solve's history and solution do not depend on the choice."""
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, "rot2d-100")
+    h = amg.amg_setup(A)
+    blk, unr = amg.amg_get_spmv_config(h)
+    assert blk in (64, 128, 256, 512) and unr in (2, 4, 8)
+    x = torch.zeros_like(b)
+    amg.amg_solve(h, b, x, 1e-8)
+    ref = (x.cpu().numpy(), amg.amg_get_history(h))
+    for blk in (64, 128, 256, 512):
+        for unr in (2, 4, 8):
+            hc = amg.amg_setup(A, spmv_block=blk, spmv_unroll=unr)
+            assert amg.amg_get_spmv_config(hc) == (blk, unr)
+            xc = torch.zeros_like(b)
+            amg.amg_solve(hc, b, xc, 1e-8)
+            assert np.array_equal(xc.cpu().numpy(), ref[0]) and np.array_equal(amg.amg_get_history(hc), ref[1])
+    with pytest.raises(amg.AmgError):
+        amg.amg_setup(A, spmv_block=96)

@@ -22,7 +22,10 @@ FGMRES (Algorithm 1 Krylov loop; stopping rule of Section 3):
   most N steps; the least-squares residual estimate equals the true residual;
 * residual estimates never increase within a cycle;
 * the AMG-preconditioned solve matches dense LU; adjoint solves A^T;
-* status codes: not converged, NaN input, zero right-hand side.
+* status codes: not converged, NaN input, zero right-hand side;
+* inner products (Dot2): equal to the exact rational value rounded to
+  nearest on well- and ill-conditioned cases, where a plain running sum is
+  far off.
 """
 import numpy as np
 import pytest
@@ -285,3 +288,43 @@ def test_status_codes(oracle_lib):
     assert info.status == O.ENUMERIC
     x, info = H.fgmres(np.zeros_like(b), x0=np.ones_like(b))
     assert info.status == O.OK and not x.any()
+
+
+def _exact_dot_rounded(a, b):
+    from fractions import Fraction
+    ex = sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b))
+    return float(ex), ex
+
+
+def test_dot2_is_correctly_rounded(oracle_lib):
+    O = oracle_lib
+    rng = np.random.default_rng(17)
+    for trial in range(60):
+        n = int(rng.integers(1, 400))
+        a, b = rng.standard_normal(n), rng.standard_normal(n) * 10.0 ** rng.integers(-8, 8)
+        ref, _ = _exact_dot_rounded(a, b)
+        assert O.dot(a, b) == ref, trial
+
+
+def test_dot2_ill_conditioned(oracle_lib):
+    """Sums that cancel to ~1e-12 of their terms: a plain running sum loses
+    most digits, Dot2 still returns the exactly rounded value."""
+    O = oracle_lib
+    rng = np.random.default_rng(18)
+    worst_plain = 0.0
+    for trial in range(40):
+        n = 200
+        big = rng.standard_normal(n // 2) * 1e6
+        a = np.concatenate([big, big])
+        b = np.concatenate([rng.standard_normal(n // 2), np.zeros(n // 2)])
+        b[n // 2:] = -b[:n // 2]                         # pairs cancel exactly ...
+        b[n // 2:] += rng.standard_normal(n // 2) * 1e-12  # ... up to a small remainder
+        perm = rng.permutation(n)
+        a, b = a[perm], b[perm]
+        ref, ex = _exact_dot_rounded(a, b)
+        assert O.dot(a, b) == ref, trial
+        plain = 0.0
+        for x, y in zip(a, b):
+            plain += x * y
+        worst_plain = max(worst_plain, abs(plain - ref) / abs(ref))
+    assert worst_plain > 1e-8          # the test cases are hard for a running sum
