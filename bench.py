@@ -202,6 +202,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SMOOTHER_PROFILE = os.path.join(ROOT, "profiles", "smoother_dram_fv3d128_one_iteration.md")
+
+
+def profiled_traffic(workload_name):
+    """DRAM bytes per smoother application from the committed ncu summary,
+    or None when the summary is for another workload or the sweep kernels'
+    source changed since it was captured."""
+    import hashlib
+    if workload_name != "c3":
+        return None
+    try:
+        lines = open(SMOOTHER_PROFILE).read().splitlines()
+    except OSError:
+        return None
+    vals = {}
+    for ln in lines:
+        if ":" in ln and ln.strip().startswith("- `"):
+            k, v = ln.strip()[3:].split("`", 1)
+            vals[k] = v.split(":", 1)[1].strip().strip("`")
+    src = os.path.join(ROOT, "paper_1105_3468_gb300", "csrc", "solve.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if vals.get("solve_cu_sha256") != sha:
+        return None
+    try:
+        return int(vals["dram_bytes_per_application"])
+    except (KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -282,8 +311,9 @@ def main():
     ap.add_argument("--bf16-steps", type=int, default=1, help="steps of the BF16-value V-cycle leg (fp32 runs)")
     ap.add_argument("--fp64-dot2", type=int, default=0, choices=[0, 1],
                     help="accurate (Dot2) inner products in the all-FP64 comparison leg (0: plain, as the mixed leg)")
-    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2],
-                    help="ILU(0) sweep schedule: 0 per-level launches, 1 level barriers, 2 dataflow")
+    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="ILU(0) sweep schedule: 0 per-level launches, 1 level barriers, 2 dataflow, "
+                         "3 dataflow on the finest level only")
     ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
     ap.add_argument("--steps-ref", type=int, default=2)
     ap.add_argument("--warmup-ref", type=int, default=0)
@@ -402,7 +432,8 @@ def main():
                  3: "CGS2 pass"}
         roof = {"bound": "hbm", "kernel": names.get(args.roofline_class), "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": "measured" if peaks else "fallback", "unit": "GB/s",
-                "frac": round(achieved / peak, 3), "traffic": None,
+                "frac": round(achieved / peak, 3),
+                "traffic": profiled_traffic(args.workload) if args.roofline_class == 2 else None,
                 "bytes_per_launch": round(tot_b / tot_n), "avg_launch_us": round(1e3 * tot_ms / tot_n, 2),
                 "launches": tot_n}
     spmv_roof = None

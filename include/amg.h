@@ -119,9 +119,11 @@ typedef struct {
                                  every application is one cooperative
                                  kernel in which each row starts when the
                                  rows it reads are written (no level
-                                 barriers; bounded waits).  All three give
+                                 barriers; bounded waits).  3: dataflow
+                                 on the finest level only, as 1 elsewhere.
+                                 All four give
                                  bit-identical results.  A wait that gives
-                                 up returns AMG_ERR_LIMIT.  Default: 1      */
+                                 up returns AMG_ERR_LIMIT.  Default: 3      */
     int32_t deep_block_max;   /* levels >= 2 with at most this many rows (and
                                  all levels below them) run their V-cycle in
                                  one thread block when deep_inner == 1;

@@ -405,7 +405,7 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
         Level &L = *Lp;
         const size_t b = tsz * (size_t)L.A.n;
         L.wt.alloc(b); L.wy.alloc(b); L.wr.alloc(b); L.wres.alloc(b); L.wh.alloc(b); L.wg.alloc(b); L.wf.alloc(b);
-        if (o.persistent == 2) {   // dataflow sweeps expect wy to hold the sentinel on entry
+        if (o.persistent >= 2) {   // dataflow sweeps expect wy to hold the sentinel on entry
             if (tsz == sizeof(double)) fill_sentinel<double>(reinterpret_cast<double *>(L.wy.get()), L.A.n, s);
             else fill_sentinel<float>(reinterpret_cast<float *>(L.wy.get()), L.A.n, s);
             L.wy_sent = (int)tsz;
@@ -504,11 +504,13 @@ struct VCycle {
         const double bytes = (sizeof(V) + 4.0) * (double)(F.v64.n + B.v64.n) + 12.0 * 2.0 * n +
                              sizeof(T) * (1.0 + (B.d64.n || F.d64.n ? 1.0 : 0.0) + 3.0) * n;
         tmark_begin(h, 2);
-        // persistent 2: dataflow solve (no level barriers) on every level;
+        // persistent 2: dataflow solve (no level barriers) on every level
+        // (3: on the finest level only, the others as with 1);
         // persistent 1: one cooperative launch with level barriers where there
         // are many schedule levels (natural order), colour classes as
         // separate launches; persistent 0: one launch per schedule level
-        if (h->opt.persistent == 2) {
+        const bool dataflow = h->opt.persistent == 2 || (h->opt.persistent == 3 && &Lv == h->lev[0].get());
+        if (dataflow) {
             if (Lv.wy_sent != (int)sizeof(T)) {
                 fill_sentinel<T>(y, (size_t)Lv.A.n, s);
                 Lv.wy_sent = (int)sizeof(T);
@@ -1038,7 +1040,7 @@ int amg_default_options(amg_options_t *o) {
     o->vcycle_prec = AMG_FP64;
     o->build_adjoint = 0;
     o->use_graphs = 1;
-    o->persistent = 1;
+    o->persistent = 3;
     o->deep_block_max = 0;
     o->orthog = AMG_ORTHO_MGS;
     o->spmv_block = 0;
@@ -1054,7 +1056,7 @@ static void check_options(const amg_options_t &o) {
         o.dense_max > 4096 || o.max_levels < 2 || o.max_levels > 24 || o.restart < 1 || o.restart > KMAX1 - 1 ||
         o.maxit < 0 || o.vcycle_prec < 0 || o.vcycle_prec > 2 || o.order_fine < 0 || o.order_fine > 1 ||
         o.order_coarse < 0 || o.order_coarse > 1 || o.coloring < 0 || o.coloring > 1 || o.deep_block_max < 0 ||
-        o.persistent < 0 || o.persistent > 2 || o.orthog < 0 || o.orthog > 1 ||
+        o.persistent < 0 || o.persistent > 3 || o.orthog < 0 || o.orthog > 1 ||
         (o.spmv_block != 0 && o.spmv_block != 64 && o.spmv_block != 128 && o.spmv_block != 256 &&
          o.spmv_block != 512) ||
         (o.spmv_unroll != 0 && o.spmv_unroll != 2 && o.spmv_unroll != 4 && o.spmv_unroll != 8) || o.dot2 < -1 ||

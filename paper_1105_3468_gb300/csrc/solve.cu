@@ -239,23 +239,63 @@ __device__ __forceinline__ void grid_barrier(unsigned int *bar, int *err) {
     __syncthreads();
 }
 
+// The same barrier split in two, so that work independent of the other
+// blocks (loading the next level's read-only data) overlaps the wait.
+// Thread 0 carries the generation from arrive to wait.
+__device__ __forceinline__ void grid_arrive(unsigned int *bar, unsigned int &gen, bool &released) {
+    __syncthreads();
+    released = false;
+    if (threadIdx.x == 0) {
+        unsigned int arrived;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+        if (arrived + 1u == gridDim.x) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(bar), "r"(0u) : "memory");
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(gen + 1u) : "memory");
+            released = true;
+        }
+    }
+}
+__device__ __forceinline__ void grid_wait(unsigned int *bar, int *err, unsigned int gen, bool released) {
+    if (threadIdx.x == 0 && !released) {
+        unsigned int spins = 0;
+        while (ld_acquire_gpu(bar + 1) == gen) {
+            if (*(volatile int *)err) break;
+            if (++spins > SPIN_LIMIT) { atomicExch(err, 1); break; }
+            if (spins > 64) __nanosleep(20);
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T> __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
 
-// Barrier between schedule levels.  SYNC 0: grid barrier of a cooperative
-// launch; 1: the grid is one thread-block cluster (hardware cluster barrier,
-// release/acquire at cluster scope); 2: the grid is one block.
+// Barrier between schedule levels, split into arrive and wait.  SYNC 0:
+// grid barrier of a cooperative launch; 1: the grid is one thread-block
+// cluster (hardware cluster barrier, release/acquire at cluster scope); 2:
+// the grid is one block.
+struct LevelSync {
+    unsigned int gen;
+    bool released;
+};
 template <int SYNC>
-__device__ __forceinline__ void level_barrier(unsigned int *bar, int *err) {
+__device__ __forceinline__ void level_arrive(unsigned int *bar, LevelSync &ls) {
     if constexpr (SYNC == 0) {
-        grid_barrier(bar, err);
+        grid_arrive(bar, ls.gen, ls.released);
     } else if constexpr (SYNC == 1) {
-        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    }
+}
+template <int SYNC>
+__device__ __forceinline__ void level_wait(unsigned int *bar, int *err, const LevelSync &ls) {
+    if constexpr (SYNC == 0) {
+        grid_wait(bar, err, ls.gen, ls.released);
+    } else if constexpr (SYNC == 1) {
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     } else {
         __syncthreads();
     }
 }
-
-
 
 // One triangular solve over all schedule levels of S.  The first row a
 // thread owns in the next level is prefetched (row id, extent, up to PF
@@ -305,17 +345,188 @@ __device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, int with_d
                 out[i] = with_diag ? a2 / S.d[t] : a2;
             }
         }
+        // the next level's row data does not depend on other blocks: load it
+        // while the barrier completes
+        const bool sync = l + 1 < S.nlev || last_barrier;
+        LevelSync ls{};
+        if (sync) level_arrive<SYNC>(bar, ls);
         prefetch(l + 1);
-        if (l + 1 < S.nlev || last_barrier) level_barrier<SYNC>(bar, err);
+        if (sync) level_wait<SYNC>(bar, err, ls);
     }
 }
 
 template <typename T, typename V, int SYNC>
 __global__ void __launch_bounds__(256) k_sweep_pair(SweepView<T, V> F, int f_diag, SweepView<T, V> B, int b_diag,
-                                                    const T *in, T *y, T *out, unsigned int *bar, int *err) {
+                                                   const T *in, T *y, T *out, unsigned int *bar, int *err) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     sweep_phase<SYNC, T, V>(F, f_diag, in, false, y, bar, err, tid, nthr, true);
     sweep_phase<SYNC, T, V>(B, b_diag, y, true, out, bar, err, tid, nthr, false);
+}
+
+// ------------------------------------------------------------------ small levels: cluster + DSMEM
+// A level whose two solve vectors (y, out) fit in shared memory runs as one
+// thread-block cluster of up to 8 CTAs.  Every CTA keeps a full copy of y
+// and out in its shared memory; a computed row value is written to all
+// copies with st.shared::cluster, and the level barrier is the cluster
+// barrier (release/acquire at cluster scope covers those writes).  Reads of
+// earlier rows are then local shared-memory loads, so a schedule level costs
+// one cluster barrier instead of a grid barrier plus L2 round trips.  Rows
+// are summed in stored order as in every other variant.
+constexpr int DSM_THREADS = 256;
+constexpr int DSM_MAX_CTAS = 8;
+constexpr size_t DSM_MAX_BYTES = 200 * 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_dsm(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_dsm(uint32_t addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// One triangular solve of the DSMEM kernel.  The first row a thread owns in
+// the next schedule level (row id, extent, the first DSM_PF terms' columns and
+// values, the diagonal, the global input) is loaded before the cluster
+// barrier, so that after it only shared-memory reads remain on the critical
+// path.  xs: the local copy read by this solve; rem: the copies written (one
+// per CTA); gout: optional global copy of the result.
+constexpr int DSM_PF = 12;
+
+template <typename T, typename V>
+__device__ __forceinline__ void dsm_phase(const SweepView<T, V> &S, const int *dl, int with_diag, const T *gin,
+                                          const T *sin, const T *xs, const uint32_t *rem, int cs, T *gout, int tid,
+                                          int nthr) {
+    int pt = -1, pi = 0, pk0 = 0, pk1 = 0, pc[DSM_PF];
+    V pv[DSM_PF];
+    T pd = T(1), pin = T(0);
+    auto prefetch = [&](int l) {
+        pt = -1;
+        if (l >= S.nlev) return;
+        const int t = dl[l] + tid;
+        if (t >= dl[l + 1]) return;
+        pt = t;
+        pi = S.rows[t];
+        pk0 = S.rp[t];
+        pk1 = S.rp[t + 1];
+#pragma unroll
+        for (int q = 0; q < DSM_PF; ++q)
+            if (pk0 + q < pk1) { pc[q] = S.ci[pk0 + q]; pv[q] = S.v[pk0 + q]; }
+        if (with_diag) pd = S.d[t];
+        if (gin) pin = gin[pi];
+    };
+    auto finish = [&](int i, T acc) {
+#pragma unroll
+        for (int r = 0; r < DSM_MAX_CTAS; ++r)
+            if (r < cs) st_dsm(rem[r] + (uint32_t)(i * sizeof(T)), acc);
+        if (gout) gout[i] = acc;
+    };
+    prefetch(0);
+    for (int l = 0; l < S.nlev; ++l) {
+        if (pt >= 0) {
+            T acc = gin ? pin : sin[pi];
+#pragma unroll
+            for (int q = 0; q < DSM_PF; ++q)
+                if (pk0 + q < pk1) acc = msub(acc, val_as<T, V>(pv[q]), xs[pc[q]]);
+            acc = row_sub<false, T, V>(acc, pk0 + DSM_PF, pk1, S.ci, S.v, xs);
+            finish(pi, with_diag ? acc / pd : acc);
+            const int e = dl[l + 1];
+            for (int t = pt + nthr; t < e; t += nthr) {      // levels wider than the cluster
+                const int i = S.rows[t];
+                T a2 = row_sub<false, T, V>(gin ? gin[i] : sin[i], S.rp[t], S.rp[t + 1], S.ci, S.v, xs);
+                finish(i, with_diag ? a2 / S.d[t] : a2);
+            }
+        }
+        // arrive, load the next level's row data, then wait; after the last
+        // level too, which keeps every CTA alive while others write to it
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        prefetch(l + 1);
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(DSM_THREADS) k_sweep_pair_dsm(SweepView<T, V> F, int f_diag, SweepView<T, V> B,
+                                                                int b_diag, const T *in, T *out, int n) {
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    T *ys = reinterpret_cast<T *>(dsm_raw);
+    T *os = ys + n;
+    int *dlf = reinterpret_cast<int *>(os + n);
+    int *dlb = dlf + F.nlev + 1;
+    for (int l = threadIdx.x; l <= F.nlev; l += DSM_THREADS) dlf[l] = F.dlev[l];
+    for (int l = threadIdx.x; l <= B.nlev; l += DSM_THREADS) dlb[l] = B.dlev[l];
+    __syncthreads();
+    const uint32_t cr = cluster_ctarank(), cs = cluster_nctarank();
+    const int tid = (int)cr * DSM_THREADS + threadIdx.x, nthr = (int)cs * DSM_THREADS;
+    uint32_t yr[DSM_MAX_CTAS], orr[DSM_MAX_CTAS];
+#pragma unroll
+    for (int r = 0; r < DSM_MAX_CTAS; ++r)
+        if (r < (int)cs) { yr[r] = map_rank(smem_u32(ys), r); orr[r] = map_rank(smem_u32(os), r); }
+    dsm_phase<T, V>(F, dlf, f_diag, in, nullptr, ys, yr, (int)cs, nullptr, tid, nthr);
+    dsm_phase<T, V>(B, dlb, b_diag, nullptr, ys, os, orr, (int)cs, out, tid, nthr);
+}
+
+// Launches the DSMEM variant when the level fits; returns false otherwise.
+template <typename T, typename V>
+static bool sweep_pair_dsm(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
+                           T *out, int maxw, cudaStream_t s) {
+    const int n = F.lev_ptr[F.nlev];
+    const size_t bytes = 2 * (size_t)n * sizeof(T) + sizeof(int) * (size_t)(F.nlev + B.nlev + 2);
+    if (n <= 0 || bytes > DSM_MAX_BYTES) return false;
+    static const bool ok = [] {               // once: opt in to large shared memory, check a full cluster fits
+        if (cudaFuncSetAttribute(k_sweep_pair_dsm<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)DSM_MAX_BYTES) != cudaSuccess)
+            return false;
+        if (cudaFuncSetAttribute(k_sweep_pair_dsm<T, V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) !=
+            cudaSuccess)
+            return false;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(DSM_MAX_CTAS);
+        cfg.blockDim = dim3(DSM_THREADS);
+        cfg.dynamicSmemBytes = DSM_MAX_BYTES;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = DSM_MAX_CTAS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_sweep_pair_dsm<T, V>, &cfg) != cudaSuccess) return false;
+        return clusters >= 1;
+    }();
+    if (!ok) { cudaGetLastError(); return false; }
+    int cs = (maxw + DSM_THREADS - 1) / DSM_THREADS;
+    cs = std::max(1, std::min(cs, DSM_MAX_CTAS));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(DSM_THREADS);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SweepView<T, V> f = F, b = B;
+    CU(cudaLaunchKernelEx(&cfg, k_sweep_pair_dsm<T, V>, f, f_diag, b, b_diag, in, out, n));
+    count_launch();
+    return true;
 }
 
 template <typename T, typename V>
@@ -329,6 +540,7 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
     int maxw = 0;
     for (int l = 0; l < F.nlev; ++l) maxw = max(maxw, F.lev_ptr[l + 1] - F.lev_ptr[l]);
     for (int l = 0; l < B.nlev; ++l) maxw = max(maxw, B.lev_ptr[l + 1] - B.lev_ptr[l]);
+    if (sweep_pair_dsm<T, V>(F, f_diag, B, b_diag, in, out, maxw, s)) return;
     int g = (maxw + 255) / 256;
     if (g > grid) g = grid;
     if (g < 1) g = 1;
