@@ -94,7 +94,8 @@ def run_batch(args, amg, torch):
             dist.barrier()
 
     def step(prec):
-        h = amg.amg_setup_batched(mats, vcycle_prec=prec, maxit=maxit)
+        extra = {"dot2": args.fp64_dot2} if prec == amg.AMG_FP64 and vp != amg.AMG_FP64 else {}
+        h = amg.amg_setup_batched(mats, vcycle_prec=prec, maxit=maxit, **extra)
         x = torch.zeros_like(b)
         st = amg.amg_solve_batched(h, b, x, tol)
         h.close()
@@ -311,9 +312,10 @@ def main():
     ap.add_argument("--bf16-steps", type=int, default=1, help="steps of the BF16-value V-cycle leg (fp32 runs)")
     ap.add_argument("--fp64-dot2", type=int, default=0, choices=[0, 1],
                     help="accurate (Dot2) inner products in the all-FP64 comparison leg (0: plain, as the mixed leg)")
-    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2, 3],
+    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="ILU(0) sweep schedule: 0 per-level launches, 1 level barriers, 2 dataflow, "
-                         "3 dataflow on the finest level only")
+                         "3 dataflow on the finest level only, 4 dataflow where the level does not fit "
+                         "the shared-memory cluster kernel")
     ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
     ap.add_argument("--steps-ref", type=int, default=2)
     ap.add_argument("--warmup-ref", type=int, default=0)

@@ -121,7 +121,9 @@ typedef struct {
                                  rows it reads are written (no level
                                  barriers; bounded waits).  3: dataflow
                                  on the finest level only, as 1 elsewhere.
-                                 All four give
+                                 4: dataflow on every level too large for
+                                 the shared-memory cluster kernel.  All
+                                 five give
                                  bit-identical results.  A wait that gives
                                  up returns AMG_ERR_LIMIT.  Default: 3      */
     int32_t deep_block_max;   /* levels >= 2 with at most this many rows (and

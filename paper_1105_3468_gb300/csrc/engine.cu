@@ -505,11 +505,13 @@ struct VCycle {
                              sizeof(T) * (1.0 + (B.d64.n || F.d64.n ? 1.0 : 0.0) + 3.0) * n;
         tmark_begin(h, 2);
         // persistent 2: dataflow solve (no level barriers) on every level
-        // (3: on the finest level only, the others as with 1);
+        // (3: on the finest level only, the others as with 1; 4: on every
+        // level too large for the shared-memory cluster kernel);
         // persistent 1: one cooperative launch with level barriers where there
         // are many schedule levels (natural order), colour classes as
         // separate launches; persistent 0: one launch per schedule level
-        const bool dataflow = h->opt.persistent == 2 || (h->opt.persistent == 3 && &Lv == h->lev[0].get());
+        const bool dataflow = h->opt.persistent == 2 || (h->opt.persistent == 3 && &Lv == h->lev[0].get()) ||
+                              (h->opt.persistent == 4 && !sweep_fits_dsm(Lv.A.n, F.nlev, B.nlev, sizeof(T)));
         if (dataflow) {
             if (Lv.wy_sent != (int)sizeof(T)) {
                 fill_sentinel<T>(y, (size_t)Lv.A.n, s);
@@ -1056,7 +1058,7 @@ static void check_options(const amg_options_t &o) {
         o.dense_max > 4096 || o.max_levels < 2 || o.max_levels > 24 || o.restart < 1 || o.restart > KMAX1 - 1 ||
         o.maxit < 0 || o.vcycle_prec < 0 || o.vcycle_prec > 2 || o.order_fine < 0 || o.order_fine > 1 ||
         o.order_coarse < 0 || o.order_coarse > 1 || o.coloring < 0 || o.coloring > 1 || o.deep_block_max < 0 ||
-        o.persistent < 0 || o.persistent > 3 || o.orthog < 0 || o.orthog > 1 ||
+        o.persistent < 0 || o.persistent > 4 || o.orthog < 0 || o.orthog > 1 ||
         (o.spmv_block != 0 && o.spmv_block != 64 && o.spmv_block != 128 && o.spmv_block != 256 &&
          o.spmv_block != 512) ||
         (o.spmv_unroll != 0 && o.spmv_unroll != 2 && o.spmv_unroll != 4 && o.spmv_unroll != 8) || o.dot2 < -1 ||

@@ -297,70 +297,118 @@ __device__ __forceinline__ void level_wait(unsigned int *bar, int *err, const Le
     }
 }
 
-// One triangular solve over all schedule levels of S.  The first row a
-// thread owns in the next level is prefetched (row id, extent, up to PF
-// columns and values, diagonal, and the input when it is not produced by this
-// launch) before the barrier, so that after the barrier only the values of
-// earlier rows remain to be loaded.
-constexpr int SWEEP_PF = 4;
+// Software pipeline over schedule levels.  A thread's row in a level is
+// read in two dependent stages: A (row id, extent, diagonal) from the
+// position, then B (the first SWEEP_PF column indices and values, and the
+// input entry) from A.  Before computing level l the thread issues B for
+// level l+1 and A for level l+2, so both loads have a whole level (compute
+// plus barrier) to arrive; only the values of earlier rows remain on the
+// critical path.  Positions beyond the first a thread owns in a level (levels
+// wider than the grid) are read directly.
+constexpr int SWEEP_PF = 8;
 constexpr int SWEEP_CLUSTER_MAX = 8;   // portable cluster size
+constexpr size_t SWEEP_DL_MAX_BYTES = 48 * 1024;   // level pointers staged in shared memory
 
-template <int SYNC, typename T, typename V>
-__device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, int with_diag, const T *in, bool in_coherent,
+template <typename T>
+struct RowA {
+    int t, i, k0, k1;
+    T d;
+};
+template <typename T, typename V>
+struct RowB {
+    int c[SWEEP_PF];
+    V v[SWEEP_PF];
+    T in;
+};
+
+template <typename T, typename V>
+__device__ __forceinline__ RowA<T> row_a(const SweepView<T, V> &S, const int *dl, int l, int tid, int with_diag) {
+    RowA<T> a{-1, 0, 0, 0, T(1)};
+    if (l >= S.nlev) return a;
+    const int t = dl[l] + tid;
+    if (t >= dl[l + 1]) return a;
+    a.t = t;
+    a.i = S.rows[t];
+    a.k0 = S.rp[t];
+    a.k1 = S.rp[t + 1];
+    if (with_diag) a.d = S.d[t];
+    return a;
+}
+
+// IN: 0 global input (plain load), 1 global input written earlier in this
+// launch (read past L1), 2 shared-memory input.
+template <int IN, typename T, typename V>
+__device__ __forceinline__ RowB<T, V> row_b(const SweepView<T, V> &S, const RowA<T> &a, const T *in) {
+    RowB<T, V> b;
+    b.in = T(0);
+    if (a.t < 0) return b;
+#pragma unroll
+    for (int q = 0; q < SWEEP_PF; ++q)
+        if (a.k0 + q < a.k1) { b.c[q] = S.ci[a.k0 + q]; b.v[q] = S.v[a.k0 + q]; }
+    b.in = IN == 1 ? __ldcg(in + a.i) : in[a.i];
+    return b;
+}
+
+// out_i = (in_i - sum_k v_k x_{c_k}) [/ d] for a pipelined row; x read past L1
+// (COHERENT) or directly (shared memory).
+template <bool COHERENT, typename T, typename V>
+__device__ __forceinline__ T row_value(const SweepView<T, V> &S, const RowA<T> &a, const RowB<T, V> &b, const T *x,
+                                       int with_diag) {
+    T xv[SWEEP_PF];
+#pragma unroll
+    for (int q = 0; q < SWEEP_PF; ++q)
+        if (a.k0 + q < a.k1) xv[q] = COHERENT ? __ldcg(x + b.c[q]) : x[b.c[q]];
+    T acc = b.in;
+#pragma unroll
+    for (int q = 0; q < SWEEP_PF; ++q)
+        if (a.k0 + q < a.k1) acc = msub(acc, val_as<T, V>(b.v[q]), xv[q]);
+    acc = row_sub<COHERENT, T, V>(acc, a.k0 + SWEEP_PF, a.k1, S.ci, S.v, x);
+    return with_diag ? acc / a.d : acc;
+}
+
+// One triangular solve over all schedule levels of S; dl: the level
+// pointers in shared memory.
+template <int SYNC, int IN, typename T, typename V>
+__device__ __forceinline__ void sweep_phase(const SweepView<T, V> &S, const int *dl, int with_diag, const T *in,
                                             T *out, unsigned int *bar, int *err, int tid, int nthr, bool last_barrier) {
-    int pt = -1, pi = 0, pk0 = 0, pk1 = 0, pc[SWEEP_PF];
-    V pv[SWEEP_PF];
-    T pd = T(1), pin = T(0);
-    auto prefetch = [&](int l) {
-        pt = -1;
-        if (l >= S.nlev) return;
-        const int t = S.dlev[l] + tid;
-        if (t >= S.dlev[l + 1]) return;
-        pt = t;
-        pi = S.rows[t];
-        pk0 = S.rp[t];
-        pk1 = S.rp[t + 1];
-#pragma unroll
-        for (int q = 0; q < SWEEP_PF; ++q)
-            if (pk0 + q < pk1) { pc[q] = S.ci[pk0 + q]; pv[q] = S.v[pk0 + q]; }
-        if (with_diag) pd = S.d[t];
-        if (!in_coherent) pin = in[pi];
-    };
-    prefetch(0);
+    RowA<T> a0 = row_a(S, dl, 0, tid, with_diag), a1 = row_a(S, dl, 1, tid, with_diag);
+    RowB<T, V> b0 = row_b<IN>(S, a0, in);
     for (int l = 0; l < S.nlev; ++l) {
-        if (pt >= 0) {
-            T acc = in_coherent ? ld_cg(in + pi) : pin;
-#pragma unroll
-            for (int q = 0; q < SWEEP_PF; ++q)
-                if (pk0 + q < pk1) acc = msub(acc, val_as<T, V>(pv[q]), ld_cg(out + pc[q]));
-            acc = row_sub<true, T, V>(acc, pk0 + SWEEP_PF, pk1, S.ci, S.v, out);
-            out[pi] = with_diag ? acc / pd : acc;
-            // further rows of this level owned by this thread (levels wider than the grid)
-            const int e = S.dlev[l + 1];
-            for (int t = pt + nthr; t < e; t += nthr) {
+        const RowB<T, V> b1 = row_b<IN>(S, a1, in);
+        const RowA<T> a2 = row_a(S, dl, l + 2, tid, with_diag);
+        if (a0.t >= 0) {
+            out[a0.i] = row_value<true, T, V>(S, a0, b0, out, with_diag);
+            const int e = dl[l + 1];
+            for (int t = a0.t + nthr; t < e; t += nthr) {
                 const int i = S.rows[t];
-                T a2 = in_coherent ? ld_cg(in + i) : in[i];
-                const int k1 = S.rp[t + 1];
-                a2 = row_sub<true, T, V>(a2, S.rp[t], k1, S.ci, S.v, out);
-                out[i] = with_diag ? a2 / S.d[t] : a2;
+                T acc = IN == 1 ? __ldcg(in + i) : in[i];
+                acc = row_sub<true, T, V>(acc, S.rp[t], S.rp[t + 1], S.ci, S.v, out);
+                out[i] = with_diag ? acc / S.d[t] : acc;
             }
         }
-        // the next level's row data does not depend on other blocks: load it
-        // while the barrier completes
-        const bool sync = l + 1 < S.nlev || last_barrier;
-        LevelSync ls{};
-        if (sync) level_arrive<SYNC>(bar, ls);
-        prefetch(l + 1);
-        if (sync) level_wait<SYNC>(bar, err, ls);
+        if (l + 1 < S.nlev || last_barrier) {
+            LevelSync ls{};
+            level_arrive<SYNC>(bar, ls);
+            level_wait<SYNC>(bar, err, ls);
+        }
+        a0 = a1;
+        b0 = b1;
+        a1 = a2;
     }
 }
 
+// Dynamic shared memory: the level pointers of F and B.
 template <typename T, typename V, int SYNC>
 __global__ void __launch_bounds__(256) k_sweep_pair(SweepView<T, V> F, int f_diag, SweepView<T, V> B, int b_diag,
                                                    const T *in, T *y, T *out, unsigned int *bar, int *err) {
+    extern __shared__ int sweep_dl[];
+    int *dlf = sweep_dl, *dlb = sweep_dl + F.nlev + 1;
+    for (int l = threadIdx.x; l <= F.nlev; l += blockDim.x) dlf[l] = F.dlev[l];
+    for (int l = threadIdx.x; l <= B.nlev; l += blockDim.x) dlb[l] = B.dlev[l];
+    __syncthreads();
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-    sweep_phase<SYNC, T, V>(F, f_diag, in, false, y, bar, err, tid, nthr, true);
-    sweep_phase<SYNC, T, V>(B, b_diag, y, true, out, bar, err, tid, nthr, false);
+    sweep_phase<SYNC, 0, T, V>(F, dlf, f_diag, in, y, bar, err, tid, nthr, true);
+    sweep_phase<SYNC, 1, T, V>(B, dlb, b_diag, y, out, bar, err, tid, nthr, false);
 }
 
 // ------------------------------------------------------------------ small levels: cluster + DSMEM
@@ -372,9 +420,11 @@ __global__ void __launch_bounds__(256) k_sweep_pair(SweepView<T, V> F, int f_dia
 // earlier rows are then local shared-memory loads, so a schedule level costs
 // one cluster barrier instead of a grid barrier plus L2 round trips.  Rows
 // are summed in stored order as in every other variant.
-constexpr int DSM_THREADS = 256;
+// threads per block: 512 for FP32 vectors, 256 for FP64 (register budget)
+template <typename T> __host__ __device__ constexpr int dsm_threads() { return sizeof(T) == 8 ? 256 : 512; }
 constexpr int DSM_MAX_CTAS = 8;
 constexpr size_t DSM_MAX_BYTES = 200 * 1024;
+constexpr int DSM_ROWS_ONE_BLOCK = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
@@ -398,85 +448,82 @@ __device__ __forceinline__ uint32_t cluster_nctarank() {
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
     return r;
 }
-// One triangular solve of the DSMEM kernel.  The first row a thread owns in
-// the next schedule level (row id, extent, the first DSM_PF terms' columns and
-// values, the diagonal, the global input) is loaded before the cluster
-// barrier, so that after it only shared-memory reads remain on the critical
-// path.  xs: the local copy read by this solve; rem: the copies written (one
-// per CTA); gout: optional global copy of the result.
-constexpr int DSM_PF = 12;
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
-template <typename T, typename V>
-__device__ __forceinline__ void dsm_phase(const SweepView<T, V> &S, const int *dl, int with_diag, const T *gin,
-                                          const T *sin, const T *xs, const uint32_t *rem, int cs, T *gout, int tid,
-                                          int nthr) {
-    int pt = -1, pi = 0, pk0 = 0, pk1 = 0, pc[DSM_PF];
-    V pv[DSM_PF];
-    T pd = T(1), pin = T(0);
-    auto prefetch = [&](int l) {
-        pt = -1;
-        if (l >= S.nlev) return;
-        const int t = dl[l] + tid;
-        if (t >= dl[l + 1]) return;
-        pt = t;
-        pi = S.rows[t];
-        pk0 = S.rp[t];
-        pk1 = S.rp[t + 1];
+// One triangular solve of the DSMEM kernel, pipelined like sweep_phase:
+// xs is the local copy read by this solve (shared memory), rem the copies
+// written (one per CTA; CLUSTER only).  The result goes to global memory
+// only at the end of the kernel, so no level barrier waits for global
+// stores.
+template <int IN, bool CLUSTER, typename T, typename V>
+__device__ __forceinline__ void dsm_phase(const SweepView<T, V> &S, const int *dl, int with_diag, const T *in, T *xs,
+                                          const uint32_t *rem, int cs, int tid, int nthr) {
+    auto finish = [&](int i, T v) {
+        if constexpr (CLUSTER) {
 #pragma unroll
-        for (int q = 0; q < DSM_PF; ++q)
-            if (pk0 + q < pk1) { pc[q] = S.ci[pk0 + q]; pv[q] = S.v[pk0 + q]; }
-        if (with_diag) pd = S.d[t];
-        if (gin) pin = gin[pi];
+            for (int r = 0; r < DSM_MAX_CTAS; ++r)
+                if (r < cs) st_dsm(rem[r] + (uint32_t)(i * sizeof(T)), v);
+        } else {
+            xs[i] = v;
+        }
     };
-    auto finish = [&](int i, T acc) {
-#pragma unroll
-        for (int r = 0; r < DSM_MAX_CTAS; ++r)
-            if (r < cs) st_dsm(rem[r] + (uint32_t)(i * sizeof(T)), acc);
-        if (gout) gout[i] = acc;
-    };
-    prefetch(0);
+    RowA<T> a0 = row_a(S, dl, 0, tid, with_diag), a1 = row_a(S, dl, 1, tid, with_diag);
+    RowB<T, V> b0 = row_b<IN>(S, a0, in);
     for (int l = 0; l < S.nlev; ++l) {
-        if (pt >= 0) {
-            T acc = gin ? pin : sin[pi];
-#pragma unroll
-            for (int q = 0; q < DSM_PF; ++q)
-                if (pk0 + q < pk1) acc = msub(acc, val_as<T, V>(pv[q]), xs[pc[q]]);
-            acc = row_sub<false, T, V>(acc, pk0 + DSM_PF, pk1, S.ci, S.v, xs);
-            finish(pi, with_diag ? acc / pd : acc);
+        const RowB<T, V> b1 = row_b<IN>(S, a1, in);
+        const RowA<T> a2 = row_a(S, dl, l + 2, tid, with_diag);
+        if (a0.t >= 0) {
+            finish(a0.i, row_value<false, T, V>(S, a0, b0, xs, with_diag));
             const int e = dl[l + 1];
-            for (int t = pt + nthr; t < e; t += nthr) {      // levels wider than the cluster
+            for (int t = a0.t + nthr; t < e; t += nthr) {      // levels wider than the grid
                 const int i = S.rows[t];
-                T a2 = row_sub<false, T, V>(gin ? gin[i] : sin[i], S.rp[t], S.rp[t + 1], S.ci, S.v, xs);
-                finish(i, with_diag ? a2 / S.d[t] : a2);
+                const T acc = row_sub<false, T, V>(in[i], S.rp[t], S.rp[t + 1], S.ci, S.v, xs);
+                finish(i, with_diag ? acc / S.d[t] : acc);
             }
         }
-        // arrive, load the next level's row data, then wait; after the last
-        // level too, which keeps every CTA alive while others write to it
-        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        prefetch(l + 1);
-        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        // after the last level too: in a cluster, keeps every CTA alive while
+        // others write to it
+        if constexpr (CLUSTER) cluster_barrier();
+        else __syncthreads();
+        a0 = a1;
+        b0 = b1;
+        a1 = a2;
     }
 }
 
-template <typename T, typename V>
-__global__ void __launch_bounds__(DSM_THREADS) k_sweep_pair_dsm(SweepView<T, V> F, int f_diag, SweepView<T, V> B,
+// Dynamic shared memory: y[n], out[n], the level pointers of F and B.
+// CLUSTER false: the grid is one block and the level barrier is the block
+// barrier (17-41 ns against ~250 ns for a cluster barrier on this GPU).
+template <typename T, typename V, bool CLUSTER>
+__global__ void __launch_bounds__(dsm_threads<T>()) k_sweep_pair_dsm(SweepView<T, V> F, int f_diag, SweepView<T, V> B,
                                                                 int b_diag, const T *in, T *out, int n) {
     extern __shared__ __align__(16) unsigned char dsm_raw[];
     T *ys = reinterpret_cast<T *>(dsm_raw);
     T *os = ys + n;
     int *dlf = reinterpret_cast<int *>(os + n);
     int *dlb = dlf + F.nlev + 1;
-    for (int l = threadIdx.x; l <= F.nlev; l += DSM_THREADS) dlf[l] = F.dlev[l];
-    for (int l = threadIdx.x; l <= B.nlev; l += DSM_THREADS) dlb[l] = B.dlev[l];
+    for (int l = threadIdx.x; l <= F.nlev; l += dsm_threads<T>()) dlf[l] = F.dlev[l];
+    for (int l = threadIdx.x; l <= B.nlev; l += dsm_threads<T>()) dlb[l] = B.dlev[l];
     __syncthreads();
-    const uint32_t cr = cluster_ctarank(), cs = cluster_nctarank();
-    const int tid = (int)cr * DSM_THREADS + threadIdx.x, nthr = (int)cs * DSM_THREADS;
+    uint32_t cr = 0, cs = 1;
     uint32_t yr[DSM_MAX_CTAS], orr[DSM_MAX_CTAS];
+    if constexpr (CLUSTER) {
+        cr = cluster_ctarank();
+        cs = cluster_nctarank();
 #pragma unroll
-    for (int r = 0; r < DSM_MAX_CTAS; ++r)
-        if (r < (int)cs) { yr[r] = map_rank(smem_u32(ys), r); orr[r] = map_rank(smem_u32(os), r); }
-    dsm_phase<T, V>(F, dlf, f_diag, in, nullptr, ys, yr, (int)cs, nullptr, tid, nthr);
-    dsm_phase<T, V>(B, dlb, b_diag, nullptr, ys, os, orr, (int)cs, out, tid, nthr);
+        for (int r = 0; r < DSM_MAX_CTAS; ++r)
+            if (r < (int)cs) { yr[r] = map_rank(smem_u32(ys), r); orr[r] = map_rank(smem_u32(os), r); }
+    }
+    const int tid = (int)cr * dsm_threads<T>() + threadIdx.x, nthr = (int)cs * dsm_threads<T>();
+    dsm_phase<0, CLUSTER, T, V>(F, dlf, f_diag, in, ys, yr, (int)cs, tid, nthr);
+    dsm_phase<2, CLUSTER, T, V>(B, dlb, b_diag, ys, os, orr, (int)cs, tid, nthr);
+    for (int i = tid; i < n; i += nthr) out[i] = os[i];     // every CTA holds all of out
+}
+
+bool sweep_fits_dsm(int n, int nlev_f, int nlev_b, size_t elem) {
+    return n > 0 && 2 * (size_t)n * elem + sizeof(int) * (size_t)(nlev_f + nlev_b + 2) <= DSM_MAX_BYTES;
 }
 
 // Launches the DSMEM variant when the level fits; returns false otherwise.
@@ -487,15 +534,14 @@ static bool sweep_pair_dsm(const SweepView<T, V> &F, int f_diag, const SweepView
     const size_t bytes = 2 * (size_t)n * sizeof(T) + sizeof(int) * (size_t)(F.nlev + B.nlev + 2);
     if (n <= 0 || bytes > DSM_MAX_BYTES) return false;
     static const bool ok = [] {               // once: opt in to large shared memory, check a full cluster fits
-        if (cudaFuncSetAttribute(k_sweep_pair_dsm<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_sweep_pair_dsm<T, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)DSM_MAX_BYTES) != cudaSuccess ||
+            cudaFuncSetAttribute(k_sweep_pair_dsm<T, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)DSM_MAX_BYTES) != cudaSuccess)
-            return false;
-        if (cudaFuncSetAttribute(k_sweep_pair_dsm<T, V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) !=
-            cudaSuccess)
             return false;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(DSM_MAX_CTAS);
-        cfg.blockDim = dim3(DSM_THREADS);
+        cfg.blockDim = dim3(dsm_threads<T>());
         cfg.dynamicSmemBytes = DSM_MAX_BYTES;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -505,26 +551,37 @@ static bool sweep_pair_dsm(const SweepView<T, V> &F, int f_diag, const SweepView
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, k_sweep_pair_dsm<T, V>, &cfg) != cudaSuccess) return false;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_sweep_pair_dsm<T, V, true>, &cfg) != cudaSuccess)
+            return false;
         return clusters >= 1;
     }();
     if (!ok) { cudaGetLastError(); return false; }
-    int cs = (maxw + DSM_THREADS - 1) / DSM_THREADS;
-    cs = std::max(1, std::min(cs, DSM_MAX_CTAS));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(DSM_THREADS);
-    cfg.dynamicSmemBytes = bytes;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    // one block (block barrier, ~20-40 ns) unless the widest level needs more
+    // than DSM_ROWS_ONE_BLOCK rows per thread; a cluster barrier costs ~0.5 us
+    // more per level, about as much as one extra row a thread reads without
+    // the pipeline
+    int cs = 1;
+    if (maxw > DSM_ROWS_ONE_BLOCK * dsm_threads<T>())
+        cs = std::min((maxw + 2 * dsm_threads<T>() - 1) / (2 * dsm_threads<T>()), DSM_MAX_CTAS);
     SweepView<T, V> f = F, b = B;
-    CU(cudaLaunchKernelEx(&cfg, k_sweep_pair_dsm<T, V>, f, f_diag, b, b_diag, in, out, n));
+    if (cs == 1) {
+        k_sweep_pair_dsm<T, V, false><<<1, dsm_threads<T>(), bytes, s>>>(f, f_diag, b, b_diag, in, out, n);
+        CU_LAUNCH("k_sweep_pair_dsm (one block)");
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(dsm_threads<T>());
+        cfg.dynamicSmemBytes = bytes;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CU(cudaLaunchKernelEx(&cfg, k_sweep_pair_dsm<T, V, true>, f, f_diag, b, b_diag, in, out, n));
+    }
     count_launch();
     return true;
 }
@@ -534,7 +591,7 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
                      T *y, T *out, unsigned int *bar, int *err, cudaStream_t s) {
     static const int grid = [] {               // initialised once, thread-safe
         int per_sm = 0;
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_pair<T, V, 0>, 256, 0));
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_pair<T, V, 0>, 256, SWEEP_DL_MAX_BYTES));
         return sm_count() * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
     }();
     int maxw = 0;
@@ -545,15 +602,21 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
     if (g > grid) g = grid;
     if (g < 1) g = 1;
     SweepView<T, V> f = F, b = B;
+    const size_t dl_bytes = sizeof(int) * (size_t)(F.nlev + B.nlev + 2);
+    if (dl_bytes > SWEEP_DL_MAX_BYTES) {          // too many schedule levels to stage: one launch per level
+        sweep<T, V>(F, in, y, f_diag, s);
+        sweep<T, V>(B, y, out, b_diag, s);
+        return;
+    }
     if (g == 1) {
-        k_sweep_pair<T, V, 2><<<1, 256, 0, s>>>(f, f_diag, b, b_diag, in, y, out, bar, err);
+        k_sweep_pair<T, V, 2><<<1, 256, dl_bytes, s>>>(f, f_diag, b, b_diag, in, y, out, bar, err);
         CU_LAUNCH("k_sweep_pair (one block)");
     } else if (g <= SWEEP_CLUSTER_MAX) {
         // a grid this small runs as one cluster: hardware barrier, all blocks co-scheduled
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(g);
         cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = 0;
+        cfg.dynamicSmemBytes = dl_bytes;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -566,7 +629,7 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
     } else {
         void *args[] = {&f, (void *)&f_diag, &b, (void *)&b_diag, (void *)&in, (void *)&y, (void *)&out, (void *)&bar,
                         (void *)&err};
-        CU(cudaLaunchCooperativeKernel((const void *)k_sweep_pair<T, V, 0>, dim3(g), dim3(256), args, 0, s));
+        CU(cudaLaunchCooperativeKernel((const void *)k_sweep_pair<T, V, 0>, dim3(g), dim3(256), args, dl_bytes, s));
     }
     count_launch();
 }

@@ -254,7 +254,7 @@ def test_graph_replay_and_persistent_identical(env):
     p, A, b, Ao, bo = _assemble(env, "aniso3d-13")
     for prec in (amg.AMG_FP64, amg.AMG_FP32, amg.AMG_BF16):
         ref = None
-        for g, pers in ((0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2), (1, 3)):
+        for g, pers in ((0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2), (1, 3), (1, 4)):
             h = amg.amg_setup(A, use_graphs=g, persistent=pers, vcycle_prec=prec)
             x = torch.zeros_like(b)
             st = amg.amg_solve(h, b, x, 1e-8)
