@@ -317,6 +317,8 @@ def main():
                          "3 dataflow on the finest level only, 4 dataflow where the level does not fit "
                          "the shared-memory cluster kernel")
     ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
+    ap.add_argument("--deep-block-max", type=int, default=None,
+                    help="levels >= 2 with at most this many rows run their V-cycle in one thread block")
     ap.add_argument("--steps-ref", type=int, default=2)
     ap.add_argument("--warmup-ref", type=int, default=0)
     args = ap.parse_args()
@@ -349,7 +351,7 @@ def main():
     torch.cuda.synchronize()
     vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
     opts = dict(sopts, maxit=maxit)
-    for k in ("persistent", "orthog"):
+    for k in ("persistent", "orthog", "deep_block_max"):
         if getattr(args, k) is not None:
             opts[k] = getattr(args, k)
 
@@ -430,7 +432,8 @@ def main():
     roof = None
     if tot_n:
         achieved = tot_b / tot_n / (tot_ms / tot_n * 1e-3) / 1e9
-        names = {1: "outer FP64 SpMV w = A z_j", 2: "ILU(0) smoother applications, all levels (k_sweep_pair/k_sweep)",
+        names = {1: "outer FP64 SpMV w = A z_j",
+                 2: "ILU(0) smoother applications, all levels (k_sweep_df / k_sweep_pair / k_sweep_pair_dsm)",
                  3: "CGS2 pass"}
         roof = {"bound": "hbm", "kernel": names.get(args.roofline_class), "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": "measured" if peaks else "fallback", "unit": "GB/s",

@@ -424,7 +424,6 @@ __global__ void __launch_bounds__(256) k_sweep_pair(SweepView<T, V> F, int f_dia
 template <typename T> __host__ __device__ constexpr int dsm_threads() { return sizeof(T) == 8 ? 256 : 512; }
 constexpr int DSM_MAX_CTAS = 8;
 constexpr size_t DSM_MAX_BYTES = 200 * 1024;
-constexpr int DSM_ROWS_ONE_BLOCK = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
@@ -556,12 +555,15 @@ static bool sweep_pair_dsm(const SweepView<T, V> &F, int f_diag, const SweepView
         return clusters >= 1;
     }();
     if (!ok) { cudaGetLastError(); return false; }
-    // one block (block barrier, ~20-40 ns) unless the widest level needs more
-    // than DSM_ROWS_ONE_BLOCK rows per thread; a cluster barrier costs ~0.5 us
-    // more per level, about as much as one extra row a thread reads without
-    // the pipeline
+    // One block (block barrier, ~20-40 ns) unless its threads would need many
+    // more row rounds than there are levels: in one block a level of w rows
+    // takes ceil(w / threads) dependent rounds, in a cluster about one round
+    // plus a cluster barrier (~0.5 us more per level).
+    int rounds = 0;
+    for (int l = 0; l < F.nlev; ++l) rounds += (F.lev_ptr[l + 1] - F.lev_ptr[l] + dsm_threads<T>() - 1) / dsm_threads<T>();
+    for (int l = 0; l < B.nlev; ++l) rounds += (B.lev_ptr[l + 1] - B.lev_ptr[l] + dsm_threads<T>() - 1) / dsm_threads<T>();
     int cs = 1;
-    if (maxw > DSM_ROWS_ONE_BLOCK * dsm_threads<T>())
+    if (2 * rounds > 3 * (F.nlev + B.nlev))
         cs = std::min((maxw + 2 * dsm_threads<T>() - 1) / (2 * dsm_threads<T>()), DSM_MAX_CTAS);
     SweepView<T, V> f = F, b = B;
     if (cs == 1) {
@@ -822,48 +824,61 @@ template void sweep_pair_df<float, __nv_bfloat16>(const SweepView<float, __nv_bf
                                                   float *, unsigned int *, int *, cudaStream_t);
 
 // ------------------------------------------------------------------ single-block deep V-cycle
+// The levels below a size threshold run their whole V-cycle (deep_inner = 1:
+// smoother, residual, restriction, the next level, prolongation) in one
+// block: a phase ends with a block barrier instead of a kernel boundary, and
+// the small vectors stay in the SM's L1 (reads after the barrier see the
+// block's own writes).  Sweeps use the same two-stage row pipeline as the
+// grid kernels.
+constexpr int DEEP_THREADS = 256;
+
 template <typename T, typename V>
-__device__ __forceinline__ void block_sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag) {
+__device__ __forceinline__ void deep_sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag) {
+    const int tid = threadIdx.x, nthr = DEEP_THREADS;
+    RowA<T> a0 = row_a(S, S.dlev, 0, tid, with_diag), a1 = row_a(S, S.dlev, 1, tid, with_diag);
+    RowB<T, V> b0 = row_b<0>(S, a0, in);
     for (int l = 0; l < S.nlev; ++l) {
-        const int b = S.dlev[l], e = S.dlev[l + 1];
-        for (int t = b + threadIdx.x; t < e; t += blockDim.x) {
-            const int i = S.rows[t];
-            T acc = in[i];
-            const int k1 = S.rp[t + 1];
-            acc = row_sub<false, T, V>(acc, S.rp[t], k1, S.ci, S.v, out);
-            out[i] = with_diag ? acc / S.d[t] : acc;
+        const RowB<T, V> b1 = row_b<0>(S, a1, in);
+        const RowA<T> a2 = row_a(S, S.dlev, l + 2, tid, with_diag);
+        if (a0.t >= 0) {
+            out[a0.i] = row_value<false, T, V>(S, a0, b0, out, with_diag);
+            const int e = S.dlev[l + 1];
+            for (int t = a0.t + nthr; t < e; t += nthr) {
+                const int i = S.rows[t];
+                const T acc = row_sub<false, T, V>(in[i], S.rp[t], S.rp[t + 1], S.ci, S.v, out);
+                out[i] = with_diag ? acc / S.d[t] : acc;
+            }
         }
         __syncthreads();
+        a0 = a1;
+        b0 = b1;
+        a1 = a2;
     }
 }
 
 template <typename T, typename V>
-__global__ void __launch_bounds__(1024) k_deep_vcycle(const DeepLevel<T, V> *L, int count) {
+__global__ void __launch_bounds__(DEEP_THREADS) k_deep_vcycle(const DeepLevel<T, V> *L, int count) {
     int m = 0;
     for (; m < count; ++m) {
         const DeepLevel<T, V> &D = L[m];
         if (D.dense) {                       // exact solve of the last level
-            for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
+            for (int i = threadIdx.x; i < D.n; i += DEEP_THREADS) {
                 double acc = 0.0;
                 const double *row = D.inv + (size_t)i * D.n;
-                for (int j = 0; j < D.n; ++j) acc += row[j] * (double)D.h[j];
+                for (int j = 0; j < D.n; ++j) acc = __fma_rn(row[j], (double)D.h[j], acc);
                 D.g[i] = (T)acc;
             }
             __syncthreads();
             break;
         }
-        block_sweep<T, V>(D.fwd, D.h, D.y, 0);
-        block_sweep<T, V>(D.bwd, D.y, D.has_child ? D.t : D.g, 1);
+        deep_sweep<T, V>(D.fwd, D.h, D.y, 0);
+        deep_sweep<T, V>(D.bwd, D.y, D.has_child ? D.t : D.g, 1);
         if (!D.has_child) break;
-        for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
-            T acc = 0;
-            const int e1 = D.rp[i + 1];
-            for (int e = D.rp[i]; e < e1; ++e) acc += val_as<T, V>(D.v[e]) * D.t[D.ci[e]];
-            D.r[i] = D.h[i] - acc;
-        }
+        for (int i = threadIdx.x; i < D.n; i += DEEP_THREADS)
+            D.r[i] = D.h[i] - row_acc<false, false, T, V>(T(0), D.rp[i], D.rp[i + 1], D.ci, D.v, D.t);
         __syncthreads();
         const DeepLevel<T, V> &C = L[m + 1];
-        for (int I = threadIdx.x; I < C.n; I += blockDim.x) {
+        for (int I = threadIdx.x; I < C.n; I += DEEP_THREADS) {
             T acc = 0;
             for (int q = D.mptr[I]; q < D.mptr[I + 1]; ++q) acc += D.r[D.midx[q]];
             C.h[I] = acc;
@@ -873,14 +888,14 @@ __global__ void __launch_bounds__(1024) k_deep_vcycle(const DeepLevel<T, V> *L, 
     for (int k = (m < count ? m : count - 1) - 1; k >= 0; --k) {
         const DeepLevel<T, V> &D = L[k];
         const DeepLevel<T, V> &C = L[k + 1];
-        for (int i = threadIdx.x; i < D.n; i += blockDim.x) D.g[i] = D.t[i] + C.g[D.agg[i]];
+        for (int i = threadIdx.x; i < D.n; i += DEEP_THREADS) D.g[i] = D.t[i] + C.g[D.agg[i]];
         __syncthreads();
     }
 }
 
 template <typename T, typename V>
 void deep_vcycle(const DeepLevel<T, V> *levels, int count, cudaStream_t s) {
-    k_deep_vcycle<T, V><<<1, 1024, 0, s>>>(levels, count);
+    k_deep_vcycle<T, V><<<1, DEEP_THREADS, 0, s>>>(levels, count);
     CU_LAUNCH("k_deep_vcycle");
     count_launch();
 }
