@@ -278,14 +278,14 @@ def run_reference(args):
         return
     vals = []
     bl = None
-    for k in range(args.warmup_ref + args.steps_ref):
+    for k in range(args.warmup + args.steps):
         bl = cpu_baseline(prob, tol, iters, sopts)
-        if k >= args.warmup_ref:
+        if k >= args.warmup:
             vals.append(bl["value"])
     v = statistics.mean(vals)
     bl["value"] = round(v, 1)
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": world,
-           "steps": args.steps_ref, "warmup": args.warmup_ref, "ms_per_step": round(v, 1),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": desc},
            "cpu_baseline": bl, "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
@@ -319,8 +319,6 @@ def main():
     ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
     ap.add_argument("--deep-block-max", type=int, default=None,
                     help="levels >= 2 with at most this many rows run their V-cycle in one thread block")
-    ap.add_argument("--steps-ref", type=int, default=2)
-    ap.add_argument("--warmup-ref", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

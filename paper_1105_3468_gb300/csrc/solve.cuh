@@ -67,8 +67,8 @@ template <typename T, typename V>
 void sweep_pair_df(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in, T *y,
                    T *out, unsigned int *bar, int *err, cudaStream_t s);
 template <typename T> void fill_sentinel(T *x, size_t n, cudaStream_t s);
-// True when a level's two solve vectors (elem bytes each) and its level
-// pointers fit the shared-memory cluster kernel.
+// True when a level's two solve vectors (elem bytes per row each) and its
+// level pointers fit the shared-memory sweep kernel.
 bool sweep_fits_dsm(int n, int nlev_f, int nlev_b, size_t elem);
 template <typename T>
 void restrict_to(int nc, const int *mptr, const int *midx, const T *r, T *h, cudaStream_t s);

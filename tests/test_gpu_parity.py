@@ -328,3 +328,30 @@ def test_spmv_autotuner_choices_identical(env):
             assert np.array_equal(xc.cpu().numpy(), ref[0]) and np.array_equal(amg.amg_get_history(hc), ref[1])
     with pytest.raises(amg.AmgError):
         amg.amg_setup(A, spmv_block=96)
+
+
+def test_shared_memory_sweep_variants_identical(env):
+    """A level just too large for the shared-memory sweep (FP64 level 0 of a
+    150^2 grid, 22,500 rows) next to coarse levels that use it: the grid,
+    shared-memory and dataflow variants all give the per-level-launch
+    result bit for bit, forward and transposed, and the FP64 V-cycle equals
+    the oracle's."""
+    amg, O, torch = env
+    p = W.c2_rotating_2d_1024(n=150)
+    A, b = amg.assemble_fv(p)
+    Ao, bo = O.fv_assemble(p)
+    z = np.random.default_rng(21).standard_normal(A.n)
+    zd = torch.as_tensor(z).cuda()
+    ref = None
+    for pers in (0, 1, 3):
+        h = amg.amg_setup(A, persistent=pers, build_adjoint=1)
+        q = torch.zeros_like(zd)
+        amg.amg_precond_apply(h, zd, q)
+        qt = torch.zeros_like(zd)
+        amg.amg_precond_apply(h, zd, qt, transpose=True)
+        cur = (q.cpu().numpy(), qt.cpu().numpy())
+        if ref is None:
+            ref = cur
+            assert np.array_equal(cur[0], O.Hierarchy(Ao).precond(z))
+        else:
+            assert np.array_equal(cur[0], ref[0]) and np.array_equal(cur[1], ref[1]), pers
