@@ -669,7 +669,16 @@ template void sweep<float, __nv_bfloat16>(const SweepView<float, __nv_bfloat16> 
 // sentinel during the forward solve and a grid barrier separates that reset
 // from the backward solve.
 constexpr unsigned int DF_SPIN_LIMIT = 1u << 20;
-constexpr int DF_LEVELS_IN_FLIGHT = 4;
+// Threads for about this many schedule levels of rows in flight, and the
+// sleep between polls of a row that is not ready (compile-time tunables).
+#ifndef AMG_DF_LEVELS_IN_FLIGHT
+#define AMG_DF_LEVELS_IN_FLIGHT 4
+#endif
+#ifndef AMG_DF_BACKOFF_NS
+#define AMG_DF_BACKOFF_NS 0
+#endif
+constexpr int DF_LEVELS_IN_FLIGHT = AMG_DF_LEVELS_IN_FLIGHT;
+constexpr unsigned int DF_BACKOFF_NS = AMG_DF_BACKOFF_NS;
 
 template <typename T> struct Sentinel;
 template <> struct Sentinel<float> {
@@ -762,8 +771,8 @@ __device__ __forceinline__ bool df_phase(const SweepView<T, V> &S, int with_diag
                 } else if ((spins & 255u) == 0 && *(volatile int *)err) {
                     fail = true;
                     done = true;
-                } else {
-                    __nanosleep(64);
+                } else if (DF_BACKOFF_NS > 0) {
+                    __nanosleep(DF_BACKOFF_NS);
                 }
             }
         }

@@ -119,3 +119,20 @@ def test_fullsize_c3_bench_configuration(env, full):
     iters = json.load(open(os.path.join(ROOT, "oracle", "workload_iters.json")))["c3"]
     print(f"128^3 FP32 V-cycle: {st.iters} iterations (FP64 oracle {iters}), true rel. residual {rel:.3e}")
     assert abs(st.iters - iters) <= 0.1 * iters
+
+
+def test_fullsize_c3_bf16_factors(env, full):
+    """BF16 ILU(0) factors on the finest level (FP32 elsewhere) inside FP64
+    FGMRES reach the true FP64 residual 1e-8 within 10% of the FP64 oracle's
+    iteration count."""
+    amg, O, torch = env
+    A, b, Ao, bo, H, opts = full("c3")
+    h = amg.amg_setup(A, vcycle_prec=amg.AMG_BF16, maxit=3000, **opts)
+    x = torch.zeros_like(b)
+    st = amg.amg_solve(h, b, x, 1e-8)
+    assert st.status == 0
+    rel = np.linalg.norm(bo - O.spmv(Ao, x.cpu().numpy())) / np.linalg.norm(bo)
+    assert rel <= 1.0000001e-8
+    iters = json.load(open(os.path.join(ROOT, "oracle", "workload_iters.json")))["c3"]
+    print(f"128^3 BF16 factors: {st.iters} iterations (FP64 oracle {iters}), true rel. residual {rel:.3e}")
+    assert abs(st.iters - iters) <= 0.1 * iters
