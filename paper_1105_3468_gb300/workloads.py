@@ -176,6 +176,40 @@ def uniform_grid(n: int, dim: int, kappa: float = 1.0, a=(0.0, 0.0, 0.0),
 
 
 # --------------------------------------------------------------------------
+# the paper's own discontinuous test cases (Section 4, test cases)
+# --------------------------------------------------------------------------
+
+def dc_kappa(n: int, dim: int) -> np.ndarray:
+    """Conductivity of the DC1 cases at the cell centres x: kappa = 1000 ([10 x_2] + 1)
+    where [10 x_i] is even for every axis i, 1 elsewhere ([.] = integer part; x_2 is the
+    second coordinate).  Isolated high-permeability zones whose value grows with x_2."""
+    c = (np.arange(n) + 0.5) / n
+    cells = np.floor(10.0 * c).astype(np.int64)
+    even = (cells % 2) == 0
+    if dim == 2:
+        ex, ey = np.meshgrid(even, even, indexing="xy")           # ex varies along x (fastest)
+        _, cy = np.meshgrid(cells, cells, indexing="xy")
+        zone = ex & ey
+        k = np.where(zone, 1000.0 * (cy + 1), 1.0)
+    else:
+        ez, ey, ex = np.meshgrid(even, even, even, indexing="ij")  # index order (z, y, x): x fastest
+        _, cy, _ = np.meshgrid(cells, cells, cells, indexing="ij")
+        zone = ex & ey & ez
+        k = np.where(zone, 1000.0 * (cy + 1), 1.0)
+    return k.reshape(-1).astype(np.float64)
+
+
+def dc_problem(n: int, dim: int, velocity: float = 0.0) -> GridProblem:
+    """DC1 (velocity 0) and DCC1 / DCC2 (a = velocity in every direction; the paper
+    uses 1000) on an n^dim grid, f = 1."""
+    k = dc_kappa(n, dim)
+    fx, fy, fz = constant_fluxes(dim, n, [velocity] * dim)
+    name = ("dcc" if velocity else "dc1") + f"-{dim}d-{n}"
+    return GridProblem(dim, n, n, n if dim == 3 else 1, k, k.copy(), k.copy(), fx, fy, fz,
+                       np.ones(n ** dim), name=name)
+
+
+# --------------------------------------------------------------------------
 # the five workloads
 # --------------------------------------------------------------------------
 

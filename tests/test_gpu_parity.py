@@ -33,6 +33,9 @@ GRID_CASES = {
     "c1-64": lambda: W.c1_block_2d_64(),
     "rot2d-100": lambda: W.c2_rotating_2d_1024(n=100),
     "aniso3d-13": lambda: W.c3_aniso_3d_128(n=13),
+    # the paper's own discontinuous cases (Section 4): DC1 2D, DCC2 3D with a = 1000
+    "dc1-2d-80": lambda: W.dc_problem(80, 2),
+    "dcc2-3d-14": lambda: W.dc_problem(14, 3, velocity=1000.0),
 }
 
 
@@ -355,3 +358,21 @@ def test_shared_memory_sweep_variants_identical(env):
             assert np.array_equal(cur[0], O.Hierarchy(Ao).precond(z))
         else:
             assert np.array_equal(cur[0], ref[0]) and np.array_equal(cur[1], ref[1]), pers
+
+
+@pytest.mark.parametrize("passes", [1, 3])
+def test_matching_passes_bit_exact(env, passes):
+    """Other numbers of matching passes per level (coarsening factor about
+    2^passes): hierarchy and FP64 history still equal the oracle's."""
+    amg, O, torch = env
+    p = W.dc_problem(80, 2, velocity=1000.0)
+    A, b = amg.assemble_fv(p)
+    Ao, bo = O.fv_assemble(p)
+    h = amg.amg_setup(A, passes=passes)
+    H = O.Hierarchy(Ao, passes=passes)
+    check_hierarchy(amg, h, H)
+    x = torch.zeros_like(b)
+    st = amg.amg_solve(h, b, x, 1e-8)
+    _, info = H.fgmres(bo, tol=1e-8)
+    assert st.status == info.status == 0 and st.iters == info.iters
+    assert np.array_equal(amg.amg_get_history(h), info.hist)
