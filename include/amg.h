@@ -65,7 +65,8 @@ extern "C" {
 /* V-cycle arithmetic (FGMRES itself always runs in FP64). */
 #define AMG_FP64 0              /* all FP64                                */
 #define AMG_FP32 1              /* FP32 storage and arithmetic             */
-#define AMG_BF16 2              /* BF16 matrix values, FP32 vectors/accum. */
+#define AMG_BF16 2              /* as FP32, with the finest level's ILU(0)
+                                   factors stored in BF16                 */
 
 /* Elimination order of the ILU(0) factors of one level. */
 #define AMG_ORDER_COLOR 0       /* colour-major (rows of a colour are independent) */
@@ -114,18 +115,20 @@ typedef struct {
     int32_t persistent;       /* ILU(0) smoother schedule.  0: one launch per
                                  schedule level.  1: an application with
                                  more than 16 schedule levels (forward +
-                                 backward) is one cooperative kernel with a
-                                 bounded grid barrier between levels.  2:
-                                 every application is one cooperative
-                                 kernel in which each row starts when the
-                                 rows it reads are written (no level
-                                 barriers; bounded waits).  3: dataflow
-                                 on the finest level only, as 1 elsewhere.
-                                 4: dataflow on every level too large for
-                                 the shared-memory cluster kernel.  All
-                                 five give
-                                 bit-identical results.  A wait that gives
-                                 up returns AMG_ERR_LIMIT.  Default: 3      */
+                                 backward) is one kernel: one block or one
+                                 cluster with both solve vectors in shared
+                                 memory when they fit, else a cooperative
+                                 grid with a bounded grid barrier between
+                                 levels.  2: every application is one
+                                 cooperative kernel in which each row
+                                 starts when the rows it reads are written
+                                 (no level barriers; bounded waits).  3:
+                                 dataflow on the finest level only, as 1
+                                 elsewhere.  4: dataflow on every level too
+                                 large for the shared-memory kernel.  All
+                                 five give bit-identical results.  A wait
+                                 that gives up returns AMG_ERR_LIMIT.
+                                 Default: 3                                 */
     int32_t deep_block_max;   /* levels >= 2 with at most this many rows (and
                                  all levels below them) run their V-cycle in
                                  one thread block when deep_inner == 1;
@@ -299,7 +302,8 @@ int amg_get_ilu(amg_handle_t *h, int32_t level, double *out);
 /* Times one kernel class with CUDA events on the handle's stream (for a
  * roofline figure measured while solving): 0 off, 1 the outer FP64 SpMV
  * w = A z_j, 2 every ILU(0) smoother application (forward + backward
- * solve) on every level, 3 one CGS2 orthogonalisation pass.  Setting
+ * solve) on every level, 3 the orthogonalisation of one column (the MGS
+ * kernel, or the first CGS2 pass).  Setting
  * a class clears the totals.  No effect on results.  Errors:
  * AMG_ERR_INVALID_ARG. */
 int amg_set_kernel_timing(amg_handle_t *h, int32_t kclass);

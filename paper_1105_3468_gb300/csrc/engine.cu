@@ -714,8 +714,9 @@ static void apply_precond_vtype(amg_handle *h, bool transpose) {
 
 // ------------------------------------------------------------------ FGMRES
 // One inner FGMRES iteration (column j = st->j, read on the device):
-// z_j = B~^{-1} v_j, w = A z_j, CGS2 against v_0..v_j, ||w||, Givens,
-// v_{j+1} = w / ||w||, and the stop flag copied to pinned host memory.
+// z_j = B~^{-1} v_j, w = A z_j, modified Gram-Schmidt (or CGS2) against
+// v_0..v_j, ||w||, Givens, v_{j+1} = w / ||w||, and the stop flag copied to
+// pinned host memory.
 // Accurate (Dot2) inner products: on by default with the FP64 V-cycle.
 static bool use_dot2(const amg_handle *h) {
     return h->opt.dot2 < 0 ? h->opt.vcycle_prec == AMG_FP64 : h->opt.dot2 != 0;

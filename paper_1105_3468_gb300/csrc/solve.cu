@@ -1,11 +1,14 @@
-// solve.cu -- solve-phase kernels: CSR SpMV and residuals, ILU(0) sweeps
-// by schedule level, restriction (segmented sum over aggregate members),
-// prolongation with correction, the dense solve of the last level, and the
-// FGMRES pieces (multi-vector dot products, CGS2 updates, Givens rotations,
-// back substitution, solution update).
+// solve.cu -- solve-phase kernels: CSR and SELL-32 SpMV and residuals, the
+// ILU(0) sweeps (per-level launches, level-barrier grid kernels, one-block
+// or cluster kernels with the vectors in shared memory, dataflow kernels),
+// restriction (segmented sum over aggregate members), prolongation with
+// correction, the dense solve of the last level, and the FGMRES pieces
+// (modified Gram-Schmidt with plain or Dot2 inner products, CGS2, Givens
+// rotations, back substitution, solution update).
 //
-// Reductions are deterministic: each block writes a partial, the last block
-// to finish (ticket counter) sums the partials in block order.
+// Reductions are deterministic: each block writes a partial, then either the
+// last block to finish (ticket counter) or every block after a grid barrier
+// sums the partials in block order.
 #include "solve.cuh"
 
 namespace amg {
