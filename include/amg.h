@@ -188,6 +188,19 @@ int amg_default_options(amg_options_t *opt);
 int amg_setup(const amg_csr_t *A, const amg_options_t *opt, void *stream,
               amg_handle_t **out);
 
+/* New values for the matrix of an existing handle, with the same sparsity
+ * pattern (val: nnz doubles in the pattern's order, host or device).  The
+ * aggregation of every level (all matching results) is kept; everything
+ * numeric is recomputed from the new values: the Galerkin products (eq. (3)),
+ * the ILU(0) factors, the dense last level, the precision copies and the
+ * transposes.  Equivalent to amg_setup on the new values with the
+ * aggregation frozen, so repeated solves with changing coefficients (an
+ * optimisation loop over the adjoint gradient) skip the matching.  If the
+ * update fails the handle keeps its previous hierarchy.
+ * Errors: AMG_ERR_INVALID_ARG (null, batched handle), AMG_ERR_BREAKDOWN
+ * (a zero pivot in the new factors), AMG_ERR_OOM, AMG_ERR_CUDA. */
+int amg_update_values(amg_handle_t *h, const double *val);
+
 /* Releases everything the handle owns.  NULL is allowed. */
 void amg_destroy(amg_handle_t *h);
 

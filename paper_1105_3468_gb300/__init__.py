@@ -29,6 +29,7 @@ __all__ = [
     "amg_status_string", "lib", "amg_set_kernel_timing", "amg_get_kernel_timing",
     "amg_launch_counter", "amg_csr_value_grad", "amg_spmv_noalloc", "amg_setup_batched",
     "amg_solve_batched", "amg_batch_size", "amg_batch_member", "amg_get_spmv_config",
+    "amg_update_values",
 ]
 
 
@@ -151,6 +152,11 @@ def amg_setup(A, opts: Optional[AmgOptions] = None, stream=None, **overrides) ->
 
 def amg_destroy(h: Handle):
     h.close()
+
+
+def amg_update_values(h: Handle, val):
+    """amg_update_values: new values on the same pattern; aggregates kept."""
+    _check(lib().amg_update_values(h.ptr, _ptr(val, "float64")), "amg_update_values")
 
 
 def amg_solve(h: Handle, b, x, tol: float = 1e-8, allow_not_converged: bool = True) -> AmgStats:

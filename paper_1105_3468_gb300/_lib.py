@@ -67,6 +67,7 @@ SIGNATURES = {
     "amg_default_options": (C.c_int, [C.POINTER(AmgOptions)]),
     "amg_setup": (C.c_int, [C.POINTER(AmgCsr), C.POINTER(AmgOptions), _P, C.POINTER(_P)]),
     "amg_destroy": (None, [_P]),
+    "amg_update_values": (C.c_int, [_P, _P]),
     "amg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.POINTER(AmgStats)]),
     "amg_adjoint": (C.c_int, [_P, _P, _P, C.c_double, C.POINTER(AmgStats)]),
     "amg_get_history": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int32)]),

@@ -131,6 +131,10 @@ __global__ void k_rp64_to_32(int n, int64_t nnz, const int64_t *rp64, int *rp32,
     }
 }
 
+__global__ void k_rp32_to_64(int n, const int *rp32, int64_t *rp64) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) rp64[i] = rp32[i];
+}
+
 static void load_csr(const amg_csr_t *A, DCsr &out, cudaStream_t s) {
     if (!A || A->n <= 0 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))
         fail(AMG_ERR_INVALID_ARG, "CSR: null pointer or non-positive size");
@@ -189,8 +193,10 @@ void build_transposed_sweeps(const DCsr &A, const int *pos, const double *lu, Sw
                              cudaStream_t s);
 
 // ------------------------------------------------------------------ setup
+// frozen: per-pass maps to reuse instead of matching (amg_update_values),
+// or nullptr.
 static void coarsen(Level &L, const amg_options_t &o, DBuf<int> &adj_rp, DBuf<int> &adj_ci, int &adj_nnz,
-                    DCsr &next, cudaStream_t s) {
+                    DCsr &next, cudaStream_t s, std::vector<PassData> *frozen = nullptr) {
     const int n = L.A.n;
     L.agg.alloc(n);
     iota_int(L.agg.get(), n, s);
@@ -203,11 +209,19 @@ static void coarsen(Level &L, const amg_options_t &o, DBuf<int> &adj_rp, DBuf<in
         DBuf<int> arp, aci;
         int annz = 0;
         sym_adjacency(*cur, arp, aci, annz, s);
-        DBuf<int> mate(cur->n);
-        match_pass(*cur, arp.get(), aci.get(), annz, o.seed, mate.get(), s);
         P.n_in = cur->n;
-        P.agg.alloc(cur->n);
-        const int nc = aggregates_from_mate(cur->n, mate.get(), P.agg.get(), s);
+        int nc = 0;
+        if (frozen) {
+            PassData &F = (*frozen)[p];
+            if (F.n_in != cur->n) fail(AMG_ERR_INVALID_ARG, "amg_update_values: hierarchy shape changed");
+            P.agg = std::move(F.agg);
+            nc = F.n_out;
+        } else {
+            DBuf<int> mate(cur->n);
+            match_pass(*cur, arp.get(), aci.get(), annz, o.seed, mate.get(), s);
+            P.agg.alloc(cur->n);
+            nc = aggregates_from_mate(cur->n, mate.get(), P.agg.get(), s);
+        }
         P.n_out = nc;
         DBuf<int> mp, mi;
         members_of(cur->n, nc, P.agg.get(), mp, mi, s);
@@ -327,7 +341,10 @@ static void tune_sell(Sell &SL, const amg_options_t &o, cudaStream_t s) {
     SL.unroll = bu;
 }
 
-static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
+// frozen (amg_update_values): the previous hierarchy's per-level, per-pass
+// maps; levels keep the same shape, only the numbers are recomputed.
+static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
+                       std::vector<std::vector<PassData>> *frozen = nullptr) {
     const amg_options_t &o = h->opt;
     cudaStream_t s = h->stream;
     auto L0 = std::make_unique<Level>();
@@ -337,12 +354,13 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain) {
     for (int l = 0;; ++l) {
         Level &L = *h->lev[l];
         bool last = (l > 0 && L.A.n <= o.dense_max) || (l + 1 >= o.max_levels);
+        if (frozen) last = l >= (int)frozen->size() || (*frozen)[l].empty();
         DBuf<int> arp, aci;
         int annz = 0;
         if (!last) {
             auto N = std::make_unique<Level>();
-            coarsen(L, o, arp, aci, annz, N->A, s);
-            if (l > 0 && (double)N->A.n > 0.9 * (double)L.A.n) {
+            coarsen(L, o, arp, aci, annz, N->A, s, frozen ? &(*frozen)[l] : nullptr);
+            if (!frozen && l > 0 && (double)N->A.n > 0.9 * (double)L.A.n) {
                 last = true;
                 L.passes.clear();
                 L.agg.release(); L.mptr.release(); L.midx.release();
@@ -1083,6 +1101,70 @@ int amg_setup(const amg_csr_t *A, const amg_options_t *opt, void *stream, amg_ha
     setup_impl(h.get(), A);
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h.release();
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_update_values(amg_handle_t *h, const double *val) {
+    ABI_TRY
+    if (!h || !val) fail(AMG_ERR_INVALID_ARG, "amg_update_values: null argument");
+    if (!h->subs.empty()) fail(AMG_ERR_INVALID_ARG, "amg_update_values: batched handle");
+    auto t0 = std::chrono::steady_clock::now();
+    CU(cudaStreamSynchronize(h->stream));
+    Level &L0 = *h->lev[0];
+    const int n = L0.A.n;
+    // copies of every level's per-pass maps: the aggregation, frozen (the
+    // handle stays intact if the update fails)
+    std::vector<std::vector<PassData>> frozen(h->lev.size());
+    for (size_t l = 0; l < h->lev.size(); ++l)
+        for (PassData &P : h->lev[l]->passes) {
+            PassData f;
+            f.agg.alloc((size_t)P.n_in);
+            CU(cudaMemcpyAsync(f.agg.get(), P.agg.get(), sizeof(int) * (size_t)P.n_in, cudaMemcpyDeviceToDevice,
+                               h->stream));
+            f.n_in = P.n_in;
+            f.n_out = P.n_out;
+            frozen[l].push_back(std::move(f));
+        }
+    CU(cudaStreamSynchronize(h->stream));
+    std::unique_ptr<amg_handle> nh(new amg_handle());
+    nh->opt = h->opt;
+    nh->ustream = h->ustream;
+    CU(cudaStreamCreateWithFlags(&nh->stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&nh->entry_ev, cudaEventDisableTiming));
+    enter(nh.get());
+    DBuf<int64_t> rp64((size_t)n + 1);
+    k_rp32_to_64<<<grid_for((size_t)n + 1, 256), 256, 0, nh->stream>>>(n, L0.A.rp.get(), rp64.get());
+    CU_LAUNCH("k_rp32_to_64"); count_launch();
+    amg_csr_t A{n, (int64_t)L0.A.nnz, rp64.get(), L0.A.ci.get(), val};
+    try {
+        setup_impl(nh.get(), &A, &frozen);
+        CU(cudaStreamSynchronize(nh->stream));
+    } catch (...) {
+        amg_destroy(nh.release());          // the handle keeps its previous hierarchy
+        throw;
+    }
+    std::swap(h->lev, nh->lev);
+    std::swap(h->n, nh->n);
+    std::swap(h->V, nh->V); std::swap(h->Zd, nh->Zd); std::swap(h->w, nh->w); std::swap(h->r, nh->r);
+    std::swap(h->xb, nh->xb); std::swap(h->bb, nh->bb); std::swap(h->hist, nh->hist);
+    std::swap(h->partials, nh->partials); std::swap(h->zin64, nh->zin64); std::swap(h->zout64, nh->zout64);
+    std::swap(h->Zf, nh->Zf); std::swap(h->zin32, nh->zin32); std::swap(h->zout32, nh->zout32);
+    std::swap(h->hflags, nh->hflags);
+    for (int d = 0; d < 2; ++d) {
+        std::swap(h->gexec[d], nh->gexec[d]);
+        std::swap(h->gpairs[d], nh->gpairs[d]);
+        std::swap(h->gnodes[d], nh->gnodes[d]);
+        std::swap(h->gbytes[d], nh->gbytes[d]);
+    }
+    std::swap(h->st, nh->st); std::swap(h->ticket, nh->ticket); std::swap(h->bar, nh->bar);
+    std::swap(h->err, nh->err); std::swap(h->hst, nh->hst);
+    std::swap(h->adjoint_ready, nh->adjoint_ready);
+    std::swap(h->deep_first, nh->deep_first);
+    std::swap(h->deep_desc, nh->deep_desc);
+    h->last_hist.clear();
+    h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    amg_destroy(nh.release());              // frees the previous hierarchy and its graphs
     return AMG_OK;
     ABI_CATCH
 }

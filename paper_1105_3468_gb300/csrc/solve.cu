@@ -1272,9 +1272,15 @@ template <bool DOT2>
 __global__ void __launch_bounds__(RT) k_norm2(size_t n, const double *__restrict__ v, double *partials,
                                               unsigned int *ticket, double *out) {
     if constexpr (DOT2) {
-        double p = 0.0, c = 0.0;
-        for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT)
+        double p = 0.0, c = 0.0, p2 = 0.0, c2 = 0.0;
+        const size_t stride = (size_t)gridDim.x * RT;
+        size_t i = blockIdx.x * (size_t)RT + threadIdx.x;
+        for (; i + stride < n; i += 2 * stride) {
             dot2_add(p, c, v[i], v[i]);
+            dot2_add(p2, c2, v[i + stride], v[i + stride]);
+        }
+        if (i < n) dot2_add(p, c, v[i], v[i]);
+        dot2_merge(p, c, p2, c2);
         block_merge2(p, c);
         if (threadIdx.x == 0) {
             partials[(size_t)blockIdx.x * KMAX1] = p;
@@ -1367,10 +1373,20 @@ __global__ void __launch_bounds__(RT) k_mgs(size_t n, FgState *st, double *w, co
         double *buf = partials + (size_t)(k & 1) * half;
         return DOT2 ? mgs_grid_sum2(p, c, buf, bar, err) : mgs_grid_sum(p, buf, bar, err);
     };
-    double p = 0.0, c = 0.0;
-    for (size_t i = tid; i < n; i += nthr) {
-        if (DOT2) dot2_add(p, c, w[i], V[i]);
-        else p = __fma_rn(w[i], V[i], p);
+    // Dot2 keeps two independent (p, c) chains per thread (even and odd
+    // elements of its stride), merged at the end, for instruction-level
+    // parallelism in the FP64 pipe.
+    double p = 0.0, c = 0.0, p2 = 0.0, c2 = 0.0;
+    if (DOT2) {
+        size_t i = tid;
+        for (; i + nthr < n; i += 2 * nthr) {
+            dot2_add(p, c, w[i], V[i]);
+            dot2_add(p2, c2, w[i + nthr], V[i + nthr]);
+        }
+        if (i < n) dot2_add(p, c, w[i], V[i]);
+        dot2_merge(p, c, p2, c2);
+    } else {
+        for (size_t i = tid; i < n; i += nthr) p = __fma_rn(w[i], V[i], p);
     }
     double h = gsum(p, c, 0);
     for (int k = 0; k <= j; ++k) {
@@ -1379,12 +1395,29 @@ __global__ void __launch_bounds__(RT) k_mgs(size_t n, FgState *st, double *w, co
         const double *vn = k < j ? V + (size_t)(k + 1) * ldv : nullptr;
         p = 0.0;
         c = 0.0;
-        for (size_t i = tid; i < n; i += nthr) {
-            const double wi = __fma_rn(-h, vk[i], w[i]);
-            w[i] = wi;
-            const double y = vn ? vn[i] : wi;
-            if (DOT2) dot2_add(p, c, wi, y);
-            else p = __fma_rn(wi, y, p);
+        if (DOT2) {
+            p2 = 0.0;
+            c2 = 0.0;
+            size_t i = tid;
+            for (; i + nthr < n; i += 2 * nthr) {
+                const double wa = __fma_rn(-h, vk[i], w[i]), wb = __fma_rn(-h, vk[i + nthr], w[i + nthr]);
+                w[i] = wa;
+                w[i + nthr] = wb;
+                dot2_add(p, c, wa, vn ? vn[i] : wa);
+                dot2_add(p2, c2, wb, vn ? vn[i + nthr] : wb);
+            }
+            if (i < n) {
+                const double wa = __fma_rn(-h, vk[i], w[i]);
+                w[i] = wa;
+                dot2_add(p, c, wa, vn ? vn[i] : wa);
+            }
+            dot2_merge(p, c, p2, c2);
+        } else {
+            for (size_t i = tid; i < n; i += nthr) {
+                const double wi = __fma_rn(-h, vk[i], w[i]);
+                w[i] = wi;
+                p = __fma_rn(wi, vn ? vn[i] : wi, p);
+            }
         }
         h = gsum(p, c, k + 1);
     }

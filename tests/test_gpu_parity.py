@@ -376,3 +376,39 @@ def test_matching_passes_bit_exact(env, passes):
     _, info = H.fgmres(bo, tol=1e-8)
     assert st.status == info.status == 0 and st.iters == info.iters
     assert np.array_equal(amg.amg_get_history(h), info.hist)
+
+
+def test_update_values_frozen_aggregation(env):
+    """amg_update_values keeps the aggregation and recomputes the numbers:
+    (1) the same values reproduce the original handle's solve bit for bit;
+    (2) scaling A by 2 leaves the heavy-edge matching unchanged, so the
+    update equals a fresh setup of 2A (compared with the oracle's hierarchy
+    of 2A, bit for bit); (3) new conductivities give a hierarchy whose
+    aggregates are the old ones and whose solve converges."""
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, "c1-64")
+    h = amg.amg_setup(A)
+    x0 = torch.zeros_like(b)
+    amg.amg_solve(h, b, x0, 1e-8)
+    ref = (x0.clone(), amg.amg_get_history(h))
+    amg.amg_update_values(h, A.val)
+    x1 = torch.zeros_like(b)
+    amg.amg_solve(h, b, x1, 1e-8)
+    assert torch.equal(x1, ref[0]) and np.array_equal(amg.amg_get_history(h), ref[1])
+    # (2) 2A: same matching, so the frozen hierarchy is the oracle's hierarchy of 2A
+    amg.amg_update_values(h, 2.0 * A.val)
+    A2 = Ao._replace(val=2.0 * Ao.val)
+    check_hierarchy(amg, h, O.Hierarchy(A2))
+    # (3) other conductivities: aggregates unchanged, solve converges on the new matrix
+    agg0 = [amg.amg_get_aggregates(h, l, 0) for l in range(amg.amg_num_levels(h) - 1)]
+    q = W.c1_block_2d_64(seed=9)
+    Aq, bq = amg.assemble_fv(q)
+    amg.amg_update_values(h, Aq.val)
+    for l, a in enumerate(agg0):
+        assert np.array_equal(amg.amg_get_aggregates(h, l, 0), a)
+    xq = torch.zeros_like(bq)
+    st = amg.amg_solve(h, bq, xq, 1e-8)
+    assert st.status == 0
+    Aqo, bqo = O.fv_assemble(q)
+    r = bqo - O.spmv(Aqo, xq.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.0000001e-8 * np.linalg.norm(bqo)
