@@ -325,6 +325,8 @@ def main():
                          "3 dataflow on the finest level only, 4 dataflow where the level does not fit "
                          "the shared-memory cluster kernel")
     ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
+    ap.add_argument("--dense-max", type=int, default=None,
+                    help="largest level (rows) solved exactly by its dense inverse")
     ap.add_argument("--deep-block-max", type=int, default=None,
                     help="levels >= 2 with at most this many rows run their V-cycle in one thread block")
     args = ap.parse_args()
@@ -357,7 +359,7 @@ def main():
     torch.cuda.synchronize()
     vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
     opts = dict(sopts, maxit=maxit)
-    for k in ("persistent", "orthog", "deep_block_max"):
+    for k in ("persistent", "orthog", "deep_block_max", "dense_max"):
         if getattr(args, k) is not None:
             opts[k] = getattr(args, k)
 

@@ -101,7 +101,9 @@ typedef struct {
     int32_t coarse_inner;     /* Richardson steps solving level 1: 5       */
     int32_t deep_inner;       /* Richardson steps on levels >= 2: 1        */
     int32_t dense_max;        /* a level with <= dense_max rows is the last
-                                 one and is solved exactly: 1024           */
+                                 one and is solved exactly (its FP64
+                                 inverse, one warp per row): 0..4096,
+                                 default 4096                               */
     int32_t max_levels;       /* 2..24, default 12                         */
     int32_t order_fine;       /* ILU(0) order of level 0: AMG_ORDER_NATURAL */
     int32_t order_coarse;     /* ILU(0) order of levels >= 1: AMG_ORDER_COLOR */

@@ -277,7 +277,7 @@ class Options(NamedTuple):
     passes: int = 2           # matching passes per level (aggregates <= 2^passes)
     coarse_inner: int = 5     # Richardson steps of the level-1 coarse solve
     deep_inner: int = 1       # Richardson steps on deeper levels
-    dense_max: int = 1024     # a level this small is solved exactly (dense inverse)
+    dense_max: int = 4096     # a level this small is solved exactly (dense inverse)
     max_levels: int = 12
     order_fine: int = ORDER_NATURAL
     order_coarse: int = ORDER_COLOR

@@ -592,8 +592,8 @@ void or_ilu_solve_t(int n, const int64_t *rp, const int32_t *ci, const double *l
 /* elimination with partial pivoting on [A | I] (pivot of column k: the  */
 /* first row of largest magnitude at or below k; the pivot row is        */
 /* divided by the pivot, then each other row i with f = m_ik != 0 gets   */
-/* m_ij - f m_kj), applied as a product with the inverse, rows summed in */
-/* column order.  a is n x n row-major (input); inv receives A^{-1}.     */
+/* m_ij - f m_kj), applied as a product with the inverse.  a is n x n    */
+/* row-major (input); inv receives A^{-1}.                               */
 /* ------------------------------------------------------------------ */
 static int dense_inverse(int n, const double *a, double *inv)
 {
@@ -629,13 +629,24 @@ static int dense_inverse(int n, const double *a, double *inv)
     return status;
 }
 
-/* x = A^{-1} b (transpose = 0) or A^{-T} b (transpose = 1) from the inverse. */
+/* x = A^{-1} b (transpose = 0) or A^{-T} b (transpose = 1) from the     */
+/* inverse.  Summation order (the paper prescribes none): the terms of   */
+/* x_i form 32 interleaved partial sums, s_r over j = r, r + 32, ... in  */
+/* ascending j with fused multiply-adds, which are then added by         */
+/* halving, s_r + s_{r+16}, then + the same at 8, 4, 2, 1.               */
 static void dense_solve(int n, const double *inv, const double *b, double *x, int transpose)
 {
     for (int i = 0; i < n; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < n; ++j) s = fma(transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j], b[j], s);
-        x[i] = s;
+        double t[32];
+        for (int r = 0; r < 32; ++r) {
+            double s = 0.0;
+            for (int j = r; j < n; j += 32)
+                s = fma(transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j], b[j], s);
+            t[r] = s;
+        }
+        for (int off = 16; off >= 1; off >>= 1)
+            for (int r = 0; r < off; ++r) t[r] = t[r] + t[r + off];
+        x[i] = t[0];
     }
 }
 

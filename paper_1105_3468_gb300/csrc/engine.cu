@@ -1051,7 +1051,7 @@ int amg_default_options(amg_options_t *o) {
     o->passes = 2;
     o->coarse_inner = 5;
     o->deep_inner = 1;
-    o->dense_max = 1024;
+    o->dense_max = 4096;
     o->max_levels = 12;
     o->order_fine = AMG_ORDER_NATURAL;
     o->order_coarse = AMG_ORDER_COLOR;

@@ -907,14 +907,16 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *M, doub
     for (int i = tid; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : M[(size_t)i * 2 * n + k];
 }
 
+// Rows over blockIdx.y, columns over x: m_ij -= f_i m_kj for i != k, f_i != 0.
 __global__ void k_gj_elim(int n, int k, double *M, const double *f) {
-    const size_t total = (size_t)n * 2 * n;
-    const double *rk = M + (size_t)k * 2 * n;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t / (2 * n)), j = (int)(t % (2 * n));
-        if (i == k) continue;
+    const int w = 2 * n;
+    const double *rk = M + (size_t)k * w;
+    for (int i = blockIdx.y; i < n; i += gridDim.y) {
         const double fi = f[i];
-        if (fi != 0.0) M[t] = __dsub_rn(M[t], __dmul_rn(fi, rk[j]));
+        if (i == k || fi == 0.0) continue;
+        double *row = M + (size_t)i * w;
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < w; j += gridDim.x * blockDim.x)
+            row[j] = __dsub_rn(row[j], __dmul_rn(fi, rk[j]));
     }
 }
 
@@ -933,7 +935,7 @@ void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
     CU(cudaMemsetAsync(bd.get(), 0, sizeof(int), s));
     k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), M.get());
     CU_LAUNCH("k_dense_from_csr"); count_launch();
-    const int eg = grid_for((size_t)n * 2 * n, 256);
+    const dim3 eg((2 * n + 255) / 256, n < 65535 ? n : 65535);
     for (int k = 0; k < n; ++k) {
         k_gj_pivot<<<1, 1024, 0, s>>>(n, k, M.get(), f.get(), bd.get());
         k_gj_elim<<<eg, 256, 0, s>>>(n, k, M.get(), f.get());

@@ -835,6 +835,25 @@ template void sweep_pair_df<float, __nv_bfloat16>(const SweepView<float, __nv_bf
                                                   const SweepView<float, __nv_bfloat16> &, int, const float *, float *,
                                                   float *, unsigned int *, int *, cudaStream_t);
 
+// ------------------------------------------------------------------ dense rows
+// Row i of a dense n x n inverse (column i for the transpose) times h, for
+// one warp: lane r sums j = r, r + 32, ... in ascending j (fused
+// multiply-add); the partial sums are added by halving (lane r + lane r + 16,
+// then 8, 4, 2, 1).  Lane 0 returns the result.
+template <typename H>
+__device__ __forceinline__ double warp_dense_dot(const double *inv, int n, int i, int transpose, int lane, H h) {
+    double s = 0.0;
+    if (transpose) {
+        for (int j = lane; j < n; j += 32) s = __fma_rn(inv[(size_t)j * n + i], h(j), s);
+    } else {
+        const double *row = inv + (size_t)i * n;
+        for (int j = lane; j < n; j += 32) s = __fma_rn(row[j], h(j), s);
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, off));
+    return s;
+}
+
 // ------------------------------------------------------------------ single-block deep V-cycle
 // The levels below a size threshold run their whole V-cycle (deep_inner = 1:
 // smoother, residual, restriction, the next level, prolongation) in one
@@ -873,12 +892,11 @@ __global__ void __launch_bounds__(DEEP_THREADS) k_deep_vcycle(const DeepLevel<T,
     int m = 0;
     for (; m < count; ++m) {
         const DeepLevel<T, V> &D = L[m];
-        if (D.dense) {                       // exact solve of the last level
-            for (int i = threadIdx.x; i < D.n; i += DEEP_THREADS) {
-                double acc = 0.0;
-                const double *row = D.inv + (size_t)i * D.n;
-                for (int j = 0; j < D.n; ++j) acc = __fma_rn(row[j], (double)D.h[j], acc);
-                D.g[i] = (T)acc;
+        if (D.dense) {                       // exact solve of the last level, one warp per row
+            const int lane = threadIdx.x & 31;
+            for (int i = threadIdx.x >> 5; i < D.n; i += DEEP_THREADS / 32) {
+                const double s = warp_dense_dot(D.inv, D.n, i, 0, lane, [&](int j) { return (double)D.h[j]; });
+                if (lane == 0) D.g[i] = (T)s;
             }
             __syncthreads();
             break;
@@ -982,21 +1000,29 @@ void convert_f32_f64(size_t n, const float *in, double *out, cudaStream_t s) {
     CU_LAUNCH("k_convert"); count_launch();
 }
 
-// Dense last level: g = Ainv h (transpose: g = Ainv^T h); one thread per
-// row, the row's terms summed in column order.
+// Dense last level: g = Ainv h (transpose: g = Ainv^T h), one warp per row
+// (h staged in shared memory as FP64).  Lane r sums the terms j = r, r + 32,
+// ... in ascending j with fused multiply-adds; the 32 partial sums are then
+// added by halving (s_r + s_{r+16}, then 8, 4, 2, 1): a fixed order, the same
+// in every variant and in the plain CPU definition.
+constexpr int DENSE_WARPS = 8;
 template <typename T>
-__global__ void k_dense_gemv(int n, const double *__restrict__ inv, const T *__restrict__ h, T *__restrict__ g,
-                             int transpose, int mode) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < n; ++j)
-            acc = madd(acc, transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j], (double)h[j]);
-        g[i] = mode ? (T)((double)g[i] + acc) : (T)acc;
+__global__ void __launch_bounds__(32 * DENSE_WARPS) k_dense_gemv(int n, const double *__restrict__ inv,
+                                                                 const T *__restrict__ h, T *__restrict__ g,
+                                                                 int transpose, int mode) {
+    extern __shared__ double dense_h[];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) dense_h[j] = (double)h[j];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * DENSE_WARPS + (threadIdx.x >> 5); i < n; i += gridDim.x * DENSE_WARPS) {
+        const double s = warp_dense_dot(inv, n, i, transpose, lane, [&](int j) { return dense_h[j]; });
+        if (lane == 0) g[i] = mode ? (T)((double)g[i] + s) : (T)s;
     }
 }
 template <typename T>
 void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, cudaStream_t s) {
-    k_dense_gemv<T><<<grid_for((size_t)n, 64), 64, 0, s>>>(n, inv, h, g, transpose, mode);
+    const int blocks = (n + DENSE_WARPS - 1) / DENSE_WARPS;
+    k_dense_gemv<T><<<blocks, 32 * DENSE_WARPS, sizeof(double) * (size_t)n, s>>>(n, inv, h, g, transpose, mode);
     CU_LAUNCH("k_dense_gemv"); count_launch();
 }
 template void dense_solve<double>(int, const double *, const double *, double *, int, int, cudaStream_t);

@@ -38,7 +38,7 @@ def test_binding_covers_header():
 def test_host_only_calls(lib):
     import paper_1105_3468_gb300 as pkg
     o = pkg.amg_default_options()
-    assert (o.passes, o.coarse_inner, o.restart, o.maxit, o.dense_max) == (2, 5, 30, 600, 1024)
+    assert (o.passes, o.coarse_inner, o.restart, o.maxit, o.dense_max) == (2, 5, 30, 600, 4096)
     assert o.order_fine == pkg.AMG_ORDER_NATURAL and o.order_coarse == pkg.AMG_ORDER_COLOR
     assert pkg.amg_status_string(pkg.AMG_ERR_NOT_CONVERGED) == "not converged"
     assert lib.amg_default_options(None) == pkg.AMG_ERR_INVALID_ARG
