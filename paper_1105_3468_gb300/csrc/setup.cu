@@ -908,6 +908,13 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *M, doub
 }
 
 // Rows over blockIdx.y, columns over x: m_ij -= f_i m_kj for i != k, f_i != 0.
+// Only columns j > k that are nonzero in the pivot row are visited.  Columns
+// j <= k of the left half are never read again (later pivots, multipliers and
+// updates use columns beyond their own step, the inverse is the right half),
+// and m_ij - f_i * (+-0) equals m_ij except possibly in the sign of a zero,
+// which no product with the inverse can see (its sums start from +0).  Half
+// the right half is still zero in the pivot row on average, so this halves
+// the traffic without changing any result.
 __global__ void k_gj_elim(int n, int k, double *M, const double *f) {
     const int w = 2 * n;
     const double *rk = M + (size_t)k * w;
@@ -915,8 +922,10 @@ __global__ void k_gj_elim(int n, int k, double *M, const double *f) {
         const double fi = f[i];
         if (i == k || fi == 0.0) continue;
         double *row = M + (size_t)i * w;
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < w; j += gridDim.x * blockDim.x)
-            row[j] = __dsub_rn(row[j], __dmul_rn(fi, rk[j]));
+        for (int j = k + 1 + blockIdx.x * blockDim.x + threadIdx.x; j < w; j += gridDim.x * blockDim.x) {
+            const double r = rk[j];
+            if (r != 0.0) row[j] = __dsub_rn(row[j], __dmul_rn(fi, r));
+        }
     }
 }
 
@@ -935,8 +944,8 @@ void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
     CU(cudaMemsetAsync(bd.get(), 0, sizeof(int), s));
     k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), M.get());
     CU_LAUNCH("k_dense_from_csr"); count_launch();
-    const dim3 eg((2 * n + 255) / 256, n < 65535 ? n : 65535);
     for (int k = 0; k < n; ++k) {
+        const dim3 eg((2 * n - k - 1 + 255) / 256, n < 65535 ? n : 65535);
         k_gj_pivot<<<1, 1024, 0, s>>>(n, k, M.get(), f.get(), bd.get());
         k_gj_elim<<<eg, 256, 0, s>>>(n, k, M.get(), f.get());
         count_launch(2);
