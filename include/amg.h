@@ -206,6 +206,23 @@ int amg_update_values(amg_handle_t *h, const double *val);
 /* Releases everything the handle owns.  NULL is allowed. */
 void amg_destroy(amg_handle_t *h);
 
+/* ILUT(tau) of a HOST CSR matrix, computed on the host: the inexact coarse
+ * factorisation A~_c = L~_c U~_c = ILUT(A_c) of Section 2 (Algorithm 1
+ * setup), with the dropping rule of Saad's ILUT (tau_i = tau * ||a_i||_2; an
+ * entry of L~ is dropped when |a_ik / u_kk| < tau_i, one of U~ when it is
+ * below tau_i; the diagonal is always kept; no cap per row), no pivoting,
+ * natural order.  tau = 0 keeps every nonzero (the complete LU without
+ * pivoting).  row_ptr [n+1] / col / val: sorted columns, diagonal present.
+ * Output, in caller-owned host arrays: f_row_ptr [n+1] and f_col / f_val
+ * [cap], row i holding its L~ part (unit diagonal implied) then its U~ part,
+ * ascending columns; *f_nnz receives the number of stored entries.
+ * Errors: AMG_ERR_INVALID_ARG (null pointer, n < 0, tau < 0 or NaN, bad CSR),
+ * AMG_ERR_LIMIT (cap < *f_nnz: nothing written but *f_nnz; call again with
+ * cap >= *f_nnz), AMG_ERR_BREAKDOWN (a zero or non-finite u_ii; the factors
+ * are still written), AMG_ERR_OOM.  Needs no GPU. */
+int amg_ilut_host(int32_t n, const int64_t *row_ptr, const int32_t *col, const double *val, double tau,
+                  int64_t cap, int64_t *f_row_ptr, int32_t *f_col, double *f_val, int64_t *f_nnz);
+
 /* --------------------------------------------------------------- solve */
 /* Solves A x = b by FGMRES(restart) preconditioned with B~ (Algorithm 1,
  * PRECONDITIONED GMRES ITERATION), stopping when the true relative residual

@@ -81,6 +81,13 @@ def lib():
             L.or_ilu0.argtypes = [C.c_int, i64p, i32p, f64p, i32p, f64p]
             L.or_ilu_solve.argtypes = [C.c_int, i64p, i32p, f64p, i32p, f64p, f64p]
             L.or_ilu_solve_t.argtypes = [C.c_int, i64p, i32p, f64p, i32p, f64p, f64p]
+            L.or_ilut.restype = vp
+            L.or_ilut.argtypes = [C.c_int, i64p, i32p, f64p, C.c_double, C.POINTER(C.c_int)]
+            L.or_ilut_nnz.restype = C.c_int64
+            L.or_ilut_nnz.argtypes = [vp]
+            L.or_ilut_get.argtypes = [vp, i64p, i32p, f64p]
+            L.or_ilut_solve.argtypes = [vp, f64p, f64p]
+            L.or_ilut_free.argtypes = [vp]
             L.or_setup.restype = vp
             L.or_setup.argtypes = [C.c_int, i64p, i32p, f64p, i32p, C.c_uint64, C.POINTER(C.c_int)]
             L.or_free.argtypes = [vp]
@@ -258,6 +265,44 @@ def ilu0(A, colors):
     lu = np.zeros(max(1, A.nnz))
     st = lib().or_ilu0(A.n, A.row_ptr, A.col, A.val, np.ascontiguousarray(colors, dtype=np.int32), lu)
     return lu[:A.nnz].copy(), st
+
+
+class Ilut:
+    """ILUT(tau) factors of A in natural order (Section 2: the inexact
+    coarse factorisation A~_c = L~_c U~_c): `F` holds row i's L~ part
+    (unit diagonal implied) and then its U~ part, ascending columns."""
+
+    def __init__(self, A, tau: float):
+        A = as_csr(A)
+        st = C.c_int(0)
+        self._h = lib().or_ilut(A.n, A.row_ptr, A.col, A.val, float(tau), C.byref(st))
+        self.status = st.value
+        if not self._h:
+            raise ValueError(f"or_ilut failed with status {st.value}")
+        nnz = int(lib().or_ilut_nnz(self._h))
+        rp = np.zeros(A.n + 1, np.int64)
+        ci = np.zeros(max(1, nnz), np.int32)
+        v = np.zeros(max(1, nnz))
+        lib().or_ilut_get(self._h, rp, ci, v)
+        self.F = Csr(A.n, rp, ci[:nnz].copy(), v[:nnz].copy())
+        self.n = A.n
+
+    def factors(self):
+        """Dense (L~, U~)."""
+        D = self.F.dense()
+        Lf = np.tril(D, -1) + np.eye(self.n)
+        return Lf, np.triu(D)
+
+    def solve(self, z):
+        t = np.zeros(self.n)
+        lib().or_ilut_solve(self._h, _f64(z), t)
+        return t
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or_ilut_free(h)
+            self._h = None
 
 
 def ilu_solve(A, lu, colors, z, transpose=False):

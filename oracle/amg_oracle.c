@@ -588,6 +588,146 @@ void or_ilu_solve_t(int n, const int64_t *rp, const int32_t *ci, const double *l
 }
 
 /* ------------------------------------------------------------------ */
+/* O5c. ILUT(tau): the incomplete factorisation with a drop tolerance   */
+/* that the paper applies to the coarse operator, A~_c = L~_c U~_c =     */
+/* ILUT(A_c) (Section 2; Algorithm 1 setup), with the dropping rule of   */
+/* Saad's ILUT and no limit on the entries per row, no pivoting (the     */
+/* paper's operators are M-matrices, for which it notes pivoting is      */
+/* rarely needed).  Natural order.  For each row i:                      */
+/*   tau_i = tau * ||a_i||_2 (sum of squares in stored column order);    */
+/*   w = a_i;                                                            */
+/*   for k < i with w_k stored, in increasing k (fill included):         */
+/*     w_k <- w_k / u_kk;  if w_k == 0 or |w_k| < tau_i drop it, else    */
+/*     w_j <- w_j - w_k * u_kj for every stored u_kj, j > k;             */
+/*   row i of L~ = the kept w_k (unit diagonal implied); row i of U~ =   */
+/*   w_i and the w_j, j > i, with w_j != 0 and |w_j| >= tau_i.           */
+/* Each product and each sum is rounded (setup arithmetic).  tau = 0     */
+/* keeps every nonzero: the complete LU factorisation without pivoting.  */
+/* Output: one CSR per row, L~ part then U~ part, ascending columns.     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int n;
+    int64_t nnz, cap;
+    int64_t *rp;        /* [n+1] */
+    int32_t *ci;
+    double *v;
+    int64_t *dpos;      /* [n] index of u_ii */
+} or_ilut_t;
+
+static void ilut_push(or_ilut_t *F, int32_t c, double x)
+{
+    if (F->nnz == F->cap) {
+        F->cap = F->cap ? 2 * F->cap : 1024;
+        F->ci = realloc(F->ci, sizeof(int32_t) * (size_t)F->cap);
+        F->v = realloc(F->v, sizeof(double) * (size_t)F->cap);
+    }
+    F->ci[F->nnz] = c;
+    F->v[F->nnz] = x;
+    F->nnz++;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+or_ilut_t *or_ilut(int n, const int64_t *rp, const int32_t *ci, const double *v, double tau, int *status)
+{
+    *status = OR_OK;
+    if (n < 0 || !(tau >= 0.0)) { *status = OR_EINVAL; return NULL; }
+    or_ilut_t *F = calloc(1, sizeof(or_ilut_t));
+    F->n = n;
+    F->rp = malloc(sizeof(int64_t) * (size_t)(n + 1));
+    F->dpos = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    double *w = calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int32_t *mark = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *lst = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));   /* stored positions of w */
+    char *done = calloc((size_t)(n > 0 ? n : 1), 1);
+    for (int j = 0; j < n; ++j) mark[j] = -1;
+    F->rp[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        double sq = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) sq = sq + v[e] * v[e];
+        const double ti = tau * sqrt(sq);
+        int len = 0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            w[ci[e]] = v[e]; mark[ci[e]] = i; lst[len++] = ci[e];
+        }
+        if (mark[i] != i) { w[i] = 0.0; mark[i] = i; lst[len++] = i; }
+        /* eliminate: the smallest unprocessed k < i each time */
+        for (;;) {
+            int k = -1;
+            for (int a = 0; a < len; ++a)
+                if (lst[a] < i && !done[lst[a]] && (k < 0 || lst[a] < k)) k = lst[a];
+            if (k < 0) break;
+            done[k] = 1;
+            double wk = w[k] / F->v[F->dpos[k]];
+            if (wk == 0.0 || fabs(wk) < ti) { w[k] = 0.0; continue; }
+            w[k] = wk;
+            for (int64_t e = F->dpos[k] + 1; e < F->rp[k + 1]; ++e) {
+                int j = F->ci[e];
+                if (mark[j] != i) { mark[j] = i; w[j] = 0.0; lst[len++] = j; }
+                w[j] = w[j] - wk * F->v[e];
+            }
+        }
+        qsort(lst, (size_t)len, sizeof(int32_t), cmp_i32);
+        for (int a = 0; a < len; ++a) {
+            int j = lst[a];
+            double x = w[j];
+            if (j < i) {
+                if (done[j] && x != 0.0) ilut_push(F, j, x);
+            } else if (j == i) {
+                F->dpos[i] = F->nnz;
+                ilut_push(F, j, x);
+                if (x == 0.0 || !isfinite(x)) *status = OR_EBREAKDOWN;
+            } else if (x != 0.0 && !(fabs(x) < ti)) {
+                ilut_push(F, j, x);
+            }
+        }
+        for (int a = 0; a < len; ++a) { done[lst[a]] = 0; w[lst[a]] = 0.0; }
+        F->rp[i + 1] = F->nnz;
+    }
+    free(w); free(mark); free(lst); free(done);
+    return F;
+}
+
+int64_t or_ilut_nnz(const or_ilut_t *F) { return F->nnz; }
+
+void or_ilut_get(const or_ilut_t *F, int64_t *rp, int32_t *ci, double *v)
+{
+    memcpy(rp, F->rp, sizeof(int64_t) * (size_t)(F->n + 1));
+    memcpy(ci, F->ci, sizeof(int32_t) * (size_t)F->nnz);
+    memcpy(v, F->v, sizeof(double) * (size_t)F->nnz);
+}
+
+/* t = (L~ U~)^{-1} z: forward then backward substitution in natural
+ * order, each row's terms accumulated in stored column order (solve
+ * phase: fused multiply-add), the backward row divided by u_ii. */
+void or_ilut_solve(const or_ilut_t *F, const double *z, double *t)
+{
+    const int n = F->n;
+    double *y = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        double s = z[i];
+        for (int64_t e = F->rp[i]; e < F->dpos[i]; ++e) s = fma(-F->v[e], y[F->ci[e]], s);
+        y[i] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int64_t e = F->dpos[i] + 1; e < F->rp[i + 1]; ++e) s = fma(-F->v[e], t[F->ci[e]], s);
+        t[i] = s / F->v[F->dpos[i]];
+    }
+    free(y);
+}
+
+void or_ilut_free(or_ilut_t *F)
+{
+    if (!F) return;
+    free(F->rp); free(F->ci); free(F->v); free(F->dpos); free(F);
+}
+
+/* ------------------------------------------------------------------ */
 /* Exact solve of the smallest level: the inverse by Gauss-Jordan        */
 /* elimination with partial pivoting on [A | I] (pivot of column k: the  */
 /* first row of largest magnitude at or below k; the pivot row is        */

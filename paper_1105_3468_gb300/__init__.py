@@ -29,7 +29,7 @@ __all__ = [
     "amg_status_string", "lib", "amg_set_kernel_timing", "amg_get_kernel_timing",
     "amg_launch_counter", "amg_csr_value_grad", "amg_spmv_noalloc", "amg_setup_batched",
     "amg_solve_batched", "amg_batch_size", "amg_batch_member", "amg_get_spmv_config",
-    "amg_update_values",
+    "amg_update_values", "amg_ilut_host",
 ]
 
 
@@ -157,6 +157,31 @@ def amg_destroy(h: Handle):
 def amg_update_values(h: Handle, val):
     """amg_update_values: new values on the same pattern; aggregates kept."""
     _check(lib().amg_update_values(h.ptr, _ptr(val, "float64")), "amg_update_values")
+
+
+def amg_ilut_host(row_ptr, col, val, tau: float):
+    """amg_ilut_host: ILUT(tau) factors of a host CSR matrix (numpy arrays:
+    int64 row pointers, int32 columns, float64 values).  Returns
+    (row_ptr, col, val, status) of the factor CSR, row i holding its L~ part
+    (unit diagonal implied) then its U~ part; status is AMG_OK or
+    AMG_ERR_BREAKDOWN."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float64)
+    n = len(rp) - 1
+    frp = np.zeros(n + 1, np.int64)
+    cap = max(1, 2 * len(ci))
+    for _ in range(2):
+        fci = np.zeros(cap, np.int32)
+        fv = np.zeros(cap, np.float64)
+        nnz = C.c_int64(0)
+        st = lib().amg_ilut_host(n, _ptr(rp), _ptr(ci), _ptr(v), float(tau), cap, _ptr(frp), _ptr(fci),
+                                 _ptr(fv), C.byref(nnz))
+        if st != AMG_ERR_LIMIT:
+            break
+        cap = int(nnz.value)
+    _check(st, "amg_ilut_host", (AMG_OK, AMG_ERR_BREAKDOWN))
+    return frp, fci[:nnz.value].copy(), fv[:nnz.value].copy(), st
 
 
 def amg_solve(h: Handle, b, x, tol: float = 1e-8, allow_not_converged: bool = True) -> AmgStats:

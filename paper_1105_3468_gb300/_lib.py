@@ -68,6 +68,8 @@ SIGNATURES = {
     "amg_setup": (C.c_int, [C.POINTER(AmgCsr), C.POINTER(AmgOptions), _P, C.POINTER(_P)]),
     "amg_destroy": (None, [_P]),
     "amg_update_values": (C.c_int, [_P, _P]),
+    "amg_ilut_host": (C.c_int, [C.c_int32, _P, _P, _P, C.c_double, C.c_int64, _P, _P, _P,
+                                C.POINTER(C.c_int64)]),
     "amg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.POINTER(AmgStats)]),
     "amg_adjoint": (C.c_int, [_P, _P, _P, C.c_double, C.POINTER(AmgStats)]),
     "amg_get_history": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int32)]),
