@@ -89,7 +89,9 @@ def lib():
             L.or_ilut_solve.argtypes = [vp, f64p, f64p]
             L.or_ilut_free.argtypes = [vp]
             L.or_setup.restype = vp
-            L.or_setup.argtypes = [C.c_int, i64p, i32p, f64p, i32p, C.c_uint64, C.POINTER(C.c_int)]
+            L.or_setup.argtypes = [C.c_int, i64p, i32p, f64p, i32p, C.c_double, C.c_uint64,
+                                   C.POINTER(C.c_int)]
+            L.or_ilut_solve_t.argtypes = [vp, f64p, f64p]
             L.or_free.argtypes = [vp]
             L.or_hier_nlev.restype = C.c_int
             L.or_hier_nlev.argtypes = [vp]
@@ -293,9 +295,9 @@ class Ilut:
         Lf = np.tril(D, -1) + np.eye(self.n)
         return Lf, np.triu(D)
 
-    def solve(self, z):
+    def solve(self, z, transpose: bool = False):
         t = np.zeros(self.n)
-        lib().or_ilut_solve(self._h, _f64(z), t)
+        (lib().or_ilut_solve_t if transpose else lib().or_ilut_solve)(self._h, _f64(z), t)
         return t
 
     def __del__(self):
@@ -315,6 +317,7 @@ def ilu_solve(A, lu, colors, z, transpose=False):
 
 # ---------------------------------------------------------------- hierarchy + solve
 ORDER_COLOR, ORDER_NATURAL = 0, 1
+COARSE_RECURSIVE, COARSE_ILUT = 0, 1
 
 
 class Options(NamedTuple):
@@ -327,6 +330,8 @@ class Options(NamedTuple):
     order_fine: int = ORDER_NATURAL
     order_coarse: int = ORDER_COLOR
     coloring: int = HASH_JP
+    coarse_solver: int = COARSE_RECURSIVE   # COARSE_ILUT: two-grid, ILUT on level 1 (Section 2)
+    ilut_tau: float = 1e-6    # drop tolerance of the ILUT two-grid (the paper's choice)
     seed: int = 0
 
 
@@ -340,9 +345,10 @@ class Hierarchy:
         self.A = as_csr(A)
         st = C.c_int(0)
         o = np.array([opts.passes, opts.coarse_inner, opts.deep_inner, opts.dense_max,
-                      opts.max_levels, opts.order_fine, opts.order_coarse, opts.coloring], np.int32)
+                      opts.max_levels, opts.order_fine, opts.order_coarse, opts.coloring,
+                      opts.coarse_solver], np.int32)
         self._h = lib().or_setup(self.A.n, self.A.row_ptr, self.A.col, self.A.val, o,
-                                 opts.seed, C.byref(st))
+                                 float(opts.ilut_tau), opts.seed, C.byref(st))
         self.status = st.value
         if not self._h:
             raise ValueError(f"or_setup failed with status {st.value}")

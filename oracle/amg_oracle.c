@@ -721,6 +721,24 @@ void or_ilut_solve(const or_ilut_t *F, const double *z, double *t)
     free(y);
 }
 
+/* t = (L~ U~)^{-T} z = L~^{-T} U~^{-T} z: U~^T w = z column by column in
+ * increasing i (divide by u_ii, then scatter -u_ij w_i to later rows),
+ * then L~^T t = w in decreasing i (scatter -l_ij t_i to earlier rows). */
+void or_ilut_solve_t(const or_ilut_t *F, const double *z, double *t)
+{
+    const int n = F->n;
+    double *w = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) w[i] = z[i];
+    for (int i = 0; i < n; ++i) {
+        w[i] = w[i] / F->v[F->dpos[i]];
+        for (int64_t e = F->dpos[i] + 1; e < F->rp[i + 1]; ++e) w[F->ci[e]] = fma(-F->v[e], w[i], w[F->ci[e]]);
+    }
+    for (int i = 0; i < n; ++i) t[i] = w[i];
+    for (int i = n - 1; i >= 0; --i)
+        for (int64_t e = F->rp[i]; e < F->dpos[i]; ++e) t[F->ci[e]] = fma(-F->v[e], t[i], t[F->ci[e]]);
+    free(w);
+}
+
 void or_ilut_free(or_ilut_t *F)
 {
     if (!F) return;
@@ -826,12 +844,15 @@ typedef struct {
     int ncol;
     double *lu;                         /* ILU(0) factors on A's layout */
     double *dense;                      /* final level: dense inverse, or NULL */
+    or_ilut_t *ilut;                    /* level 1 of the ILUT two-grid, or NULL */
 } or_level_t;
 
 typedef struct {
     int nlev;
     or_level_t lev[OR_MAX_LEVELS];
     int passes, coarse_inner, deep_inner, dense_max, order_fine, order_coarse, coloring;
+    int coarse_ilut;                    /* 1: two-grid, level 1 factored by ILUT(ilut_tau) */
+    double ilut_tau;
     uint64_t seed;
     int status;
 } or_hier_t;
@@ -857,6 +878,7 @@ void or_free(or_hier_t *H)
         csr_free(&L->A);
         for (int p = 0; p < OR_MAX_PASSES; ++p) { csr_free(&L->mid[p]); free(L->agg_pass[p]); }
         free(L->agg); free(L->color); free(L->lu); free(L->dense);
+        or_ilut_free(L->ilut);
     }
     free(H);
 }
@@ -892,21 +914,28 @@ static void coarsen_level(or_level_t *L, int passes, uint64_t seed, or_csr_t *ne
 }
 
 or_hier_t *or_setup(int n, const int64_t *rp, const int32_t *ci, const double *v,
-                    const int32_t *opt, uint64_t seed, int *status)
+                    const int32_t *opt, double ilut_tau, uint64_t seed, int *status)
 {
     /* opt: [passes, coarse_inner, deep_inner, dense_max, max_levels,
-     *       order_fine, order_coarse, coloring]
-     * order: 0 = colour-major (hash or first-fit colouring), 1 = natural. */
+     *       order_fine, order_coarse, coloring, coarse_solver]
+     * order: 0 = colour-major (hash or first-fit colouring), 1 = natural.
+     * coarse_solver: 0 = the recursive Richardson coarse solve; 1 = the
+     * paper's two-grid form (Section 2, Algorithm 1): level 1 is the last
+     * one, factored once by ILUT(ilut_tau) and solved with its factors. */
     *status = OR_OK;
     int passes = opt[0], coarse_inner = opt[1], deep_inner = opt[2], dense_max = opt[3];
     int max_levels = opt[4], order_fine = opt[5], order_coarse = opt[6], coloring = opt[7];
+    int coarse_ilut = opt[8];
+    if (coarse_ilut) max_levels = 2;
     if (n <= 0 || passes < 1 || passes > OR_MAX_PASSES || coarse_inner < 1 || deep_inner < 1 ||
-        dense_max < 0 || max_levels < 2 || max_levels > OR_MAX_LEVELS) { *status = OR_EINVAL; return NULL; }
+        dense_max < 0 || max_levels < 2 || max_levels > OR_MAX_LEVELS || coarse_ilut < 0 || coarse_ilut > 1 ||
+        (coarse_ilut && !(ilut_tau >= 0.0))) { *status = OR_EINVAL; return NULL; }
     if (or_check_csr(n, rp, ci) != OR_OK) { *status = OR_EINVAL; return NULL; }
     or_hier_t *H = calloc(1, sizeof(or_hier_t));
     H->passes = passes; H->coarse_inner = coarse_inner; H->deep_inner = deep_inner;
     H->dense_max = dense_max; H->order_fine = order_fine; H->order_coarse = order_coarse;
     H->coloring = coloring; H->seed = seed;
+    H->coarse_ilut = coarse_ilut; H->ilut_tau = ilut_tau;
     csr_copy(&H->lev[0].A, n, rp, ci, v);
     H->nlev = 1;
     for (int l = 0; ; ++l) {
@@ -927,7 +956,11 @@ or_hier_t *or_setup(int n, const int64_t *rp, const int32_t *ci, const double *v
             }
         }
         int m = L->A.n;
-        if (last && m <= dense_max) {
+        if (coarse_ilut && l == 1) {
+            int st = OR_OK;
+            L->ilut = or_ilut(m, L->A.rp, L->A.ci, L->A.v, ilut_tau, &st);
+            if (st != OR_OK) *status = st;
+        } else if (last && m <= dense_max) {
             double *a = calloc((size_t)m * (size_t)m, sizeof(double));
             L->dense = malloc(sizeof(double) * (size_t)m * (size_t)m);
             for (int i = 0; i < m; ++i)
@@ -1025,7 +1058,8 @@ void or_hier_lu(const or_hier_t *H, int l, double *out)
 /*   h[I] = sum_{i in G_I} r_i        restriction P^T (i ascending)      */
 /*   g = C_{l+1}(h)                   inexact coarse solve               */
 /*   q_i = t_i + g[agg_i]             prolongation P and correction      */
-/* C_m(h): product with the inverse on a dense final level; k_m          */
+/* C_m(h): product with the inverse on a dense final level; one solve    */
+/* with the ILUT factors in the two-grid form; k_m                       */
 /* Richardson steps with S_m^{-1} on a final level without it; else k_m  */
 /* Richardson steps g <- g + B_m^{-1}(h - A_m g) from g = 0.             */
 /* ------------------------------------------------------------------ */
@@ -1051,6 +1085,11 @@ void or_level_solve(const or_hier_t *H, int l, const double *h, double *g, int t
     const or_level_t *L = &H->lev[l];
     int m = L->A.n;
     if (L->dense) { dense_solve(m, L->dense, h, g, transpose); return; }
+    if (L->ilut) {                       /* A~_c^{-1} h with the ILUT factors */
+        if (transpose) or_ilut_solve_t(L->ilut, h, g);
+        else or_ilut_solve(L->ilut, h, g);
+        return;
+    }
     int k = (l == 1) ? H->coarse_inner : H->deep_inner;
     double *res = malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     double *d = malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));

@@ -15,7 +15,13 @@ with Saad's dropping rule (tau_i = tau * ||a_i||_2) and no pivoting:
 * the triangular solve with the factors equals the dense solve with L~U~;
 * on the 64^2 block-kappa operator, fewer entries are kept and the relative
   factorisation error ||A - L~U~|| / ||A|| grows as tau grows (the trend
-  of the paper's Table of ||LU - L~U~|| / ||LU||, context only).
+  of the paper's Table of ||LU - L~U~|| / ||LU||, context only);
+* a hand-computed 3x3 case in which one fill entry is kept at tau = 0.01
+  and dropped at tau = 0.02.
+The two-grid form of Algorithm 1 with this coarse factorisation (one solve
+with L~_c U~_c, level 1 the last level): with tau = 0 it equals the two-grid
+preconditioner with the exact coarse inverse; its transpose is the
+transpose; its coarse solve is the factor solve.
 """
 import numpy as np
 import pytest
@@ -121,3 +127,40 @@ def test_hand_computed_3x3(oracle_lib, tau, kept):
         assert Uf[2, 2] == pytest.approx(3.75 - 1 / 60, rel=1e-15)
     else:
         assert Lf[2, 1] == 0.0 and Uf[2, 2] == 3.75
+
+
+def _small(O):
+    p = W.block_kappa_grid(16, 2, 4, -2, 2, 31, velocity=("const", (1.0, 0.5)))
+    return O.fv_assemble(p)
+
+
+def test_two_grid_with_ilut_tau0_is_the_exact_two_grid(oracle_lib):
+    """The paper's two-grid form (Algorithm 1: A~_c = ILUT(A_c), one coarse
+    solve): with tau = 0 the coarse factors are exact, so the preconditioner
+    equals the two-grid one whose coarse level is solved by its inverse."""
+    O = oracle_lib
+    A, _ = _small(O)
+    Hi = O.Hierarchy(A, coarse_solver=O.COARSE_ILUT, ilut_tau=0.0)
+    He = O.Hierarchy(A, dense_max=10 ** 6, max_levels=2)
+    assert Hi.nlev == He.nlev == 2 and He.levels[1]["dense"] and not Hi.levels[1]["dense"]
+    z = np.random.default_rng(8).standard_normal(A.n)
+    for tr in (False, True):
+        qi, qe = Hi.precond(z, transpose=tr), He.precond(z, transpose=tr)
+        assert np.allclose(qi, qe, rtol=1e-10, atol=1e-12 * np.abs(qe).max())
+
+
+def test_two_grid_with_ilut_transpose_and_coarse_solve(oracle_lib):
+    O = oracle_lib
+    A, _ = _small(O)
+    H = O.Hierarchy(A, coarse_solver=O.COARSE_ILUT, ilut_tau=1e-3)
+    n = A.n
+    Bi = np.column_stack([H.precond(e) for e in np.eye(n)])
+    BiT = np.column_stack([H.precond(e, transpose=True) for e in np.eye(n)])
+    assert np.allclose(BiT, Bi.T, rtol=1e-10, atol=1e-12 * np.abs(Bi).max())
+    A1 = H.matrix(1)
+    I = O.Ilut(A1, 1e-3)
+    h = np.random.default_rng(9).standard_normal(A1.n)
+    assert np.array_equal(H.level_solve(1, h), I.solve(h))
+    assert np.array_equal(H.level_solve(1, h, transpose=True), I.solve(h, transpose=True))
+    Lf, Uf = I.factors()
+    assert np.allclose(I.solve(h, transpose=True), np.linalg.solve((Lf @ Uf).T, h), rtol=1e-9)
