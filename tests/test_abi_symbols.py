@@ -51,5 +51,5 @@ def test_host_only_calls(lib):
 
 def test_struct_sizes_match_header():
     from paper_1105_3468_gb300 import _lib
-    assert C.sizeof(_lib.AmgOptions) == 20 * 4 + 8
+    assert C.sizeof(_lib.AmgOptions) == 20 * 4 + 8 + 2 * 4 + 8
     assert C.sizeof(_lib.AmgStats) == 4 * 4 + 3 * 8 + 2 * 4 + 2 * 8
