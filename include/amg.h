@@ -76,6 +76,14 @@ extern "C" {
 #define AMG_COLOR_HASH_JP 0     /* priority (mix64(i ^ (seed + 0x9e3779b97f4a7c15)), i) */
 #define AMG_COLOR_FIRST_FIT 1   /* priority -i (first fit in index order)  */
 
+/* Coarse solve of level 1 (amg_options_t.coarse_solver). */
+#define AMG_COARSE_RECURSIVE 0  /* coarse_inner Richardson steps, each
+                                   preconditioned by the same two-grid
+                                   construction on the coarse level        */
+#define AMG_COARSE_ILUT 1       /* the paper's two-grid form: level 1 is the
+                                   last level, factored once by ILUT(ilut_tau)
+                                   (Section 2) and solved with its factors  */
+
 /* Orthogonalisation of the outer FGMRES (Arnoldi process). */
 #define AMG_ORTHO_MGS 0         /* modified Gram-Schmidt                   */
 #define AMG_ORTHO_CGS2 1        /* classical Gram-Schmidt, two passes      */
@@ -154,6 +162,12 @@ typedef struct {
                                  -1 = on with the FP64 V-cycle only: -1    */
     int32_t reserved0;        /* 0                                         */
     uint64_t seed;            /* tie-break seed, default 0                 */
+    int32_t coarse_solver;    /* AMG_COARSE_RECURSIVE (default) or
+                                 AMG_COARSE_ILUT                           */
+    int32_t reserved1;        /* 0                                         */
+    double ilut_tau;          /* drop tolerance of AMG_COARSE_ILUT (the
+                                 factorisation of amg_ilut_host): >= 0,
+                                 default 1e-6                               */
 } amg_options_t;
 
 typedef struct {

@@ -16,7 +16,7 @@ from typing import Optional
 import numpy as np
 
 from . import _lib
-from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_ORTHO_CGS2, AMG_ORTHO_MGS, AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
+from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_COARSE_ILUT, AMG_COARSE_RECURSIVE, AMG_ORTHO_CGS2, AMG_ORTHO_MGS, AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
                    AMG_ERR_CUDA, AMG_ERR_INVALID_ARG, AMG_ERR_LIMIT, AMG_ERR_NOT_CONVERGED,
                    AMG_ERR_NOT_SUPPORTED, AMG_ERR_NUMERIC, AMG_ERR_OOM, AMG_FP32, AMG_FP64, AMG_OK,
                    AMG_ORDER_COLOR, AMG_ORDER_NATURAL, AmgCsr, AmgOptions, AmgStats)
@@ -100,13 +100,17 @@ def amg_status_string(st: int) -> str:
     return lib().amg_status_string(st).decode()
 
 
+def _set_option(o: AmgOptions, k: str, v):
+    if not hasattr(o, k):
+        raise KeyError(k)
+    setattr(o, k, float(v) if k == "ilut_tau" else int(v))
+
+
 def amg_default_options(**overrides) -> AmgOptions:
     o = AmgOptions()
     _check(lib().amg_default_options(C.byref(o)), "amg_default_options")
     for k, v in overrides.items():
-        if not hasattr(o, k):
-            raise KeyError(k)
-        setattr(o, k, int(v))
+        _set_option(o, k, v)
     return o
 
 
@@ -141,7 +145,7 @@ def amg_setup(A, opts: Optional[AmgOptions] = None, stream=None, **overrides) ->
     """amg_setup: build the hierarchy of A (object with n, row_ptr, col, val)."""
     o = opts if opts is not None else amg_default_options()
     for k, v in overrides.items():
-        setattr(o, k, int(v))
+        _set_option(o, k, v)
     cs = _csr(A)
     if stream is None:
         stream = _stream_of(A.row_ptr, A.val)
@@ -206,7 +210,7 @@ def amg_setup_batched(systems, opts: Optional[AmgOptions] = None, stream=None, *
     """amg_setup_batched: one hierarchy per system (list of CSR objects)."""
     o = opts if opts is not None else amg_default_options()
     for k, v in overrides.items():
-        setattr(o, k, int(v))
+        _set_option(o, k, v)
     arr = (AmgCsr * len(systems))(*[_csr(A) for A in systems])
     if stream is None:
         stream = _stream_of(systems[0].row_ptr)

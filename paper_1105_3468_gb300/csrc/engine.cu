@@ -46,6 +46,9 @@ struct Level {
     DBuf<int> label, pos;
     DBuf<double> lu;
     Sweep fwd, bwd, fwdT, bwdT;
+    // level 1 of the ILUT two-grid: the factors' pattern (values in lu)
+    bool ilut_level = false;
+    DCsr fpat;
     // dense last level
     bool dense = false;
     DBuf<double> inv;
@@ -268,6 +271,48 @@ static void build_smoother(Level &L, int order, const amg_options_t &o, const in
     ilu0_factor(L.A, L.pos.get(), L.lu, L.fwd, L.bwd, s);
 }
 
+// Level 1 of the paper's two-grid form (Section 2, Algorithm 1 setup):
+// A~_c = ILUT(A_c) on the host, the factors uploaded with their own pattern
+// and scheduled for the same triangular sweeps as ILU(0) (natural order).
+static void build_ilut_level(Level &L, const amg_options_t &o, cudaStream_t s) {
+    const int n = L.A.n;
+    std::vector<int> hrp(n + 1), hci(L.A.nnz);
+    std::vector<double> hv(L.A.nnz);
+    CU(cudaMemcpyAsync(hrp.data(), L.A.rp.get(), sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(hci.data(), L.A.ci.get(), sizeof(int) * L.A.nnz, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(hv.data(), L.A.v.get(), sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    std::vector<int64_t> rp64(hrp.begin(), hrp.end());
+    std::vector<int64_t> frp;
+    std::vector<int32_t> fci;
+    std::vector<double> fv;
+    if (!ilut_factor_host(n, rp64.data(), hci.data(), hv.data(), o.ilut_tau, frp, fci, fv))
+        fail(AMG_ERR_BREAKDOWN, "ILUT of the coarse level: zero or non-finite pivot");
+    const int64_t nnz = frp[n];
+    if (nnz >= (int64_t)0x7fffffff) fail(AMG_ERR_INVALID_ARG, "ILUT of the coarse level: factors with >= 2^31 entries");
+    std::vector<int> frp32(frp.begin(), frp.end());
+    DCsr &F = L.fpat;
+    F.n = n;
+    F.nnz = (int)nnz;
+    F.rp.alloc(n + 1);
+    F.ci.alloc(nnz > 0 ? nnz : 1);
+    F.v.alloc(nnz > 0 ? nnz : 1);
+    CU(cudaMemcpyAsync(F.rp.get(), frp32.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(F.ci.get(), fci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(F.v.get(), fv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    L.lu.alloc(nnz > 0 ? nnz : 1);
+    CU(cudaMemcpyAsync(L.lu.get(), fv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    L.order = AMG_ORDER_NATURAL;
+    L.ncol = 0;
+    L.label.alloc(n);
+    L.pos.alloc(n);
+    fill_int(L.label.get(), 0, n, s);
+    elimination_positions(n, L.label.get(), 1, L.pos.get(), s);
+    factor_sweeps(F, L.pos.get(), L.lu.get(), L.fwd, L.bwd, s);
+    CU(cudaStreamSynchronize(s));   // the host vectors above are the copies' sources
+    L.ilut_level = true;
+}
+
 static void cast_sweep(Sweep &S, int prec, cudaStream_t s) {
     const size_t nnzf = S.v64.n;
     if (prec == AMG_FP32 || prec == AMG_BF16) {
@@ -353,7 +398,8 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
     h->lev.push_back(std::move(L0));
     for (int l = 0;; ++l) {
         Level &L = *h->lev[l];
-        bool last = (l > 0 && L.A.n <= o.dense_max) || (l + 1 >= o.max_levels);
+        const bool two_grid = o.coarse_solver == AMG_COARSE_ILUT;
+        bool last = two_grid ? l >= 1 : ((l > 0 && L.A.n <= o.dense_max) || (l + 1 >= o.max_levels));
         if (frozen) last = l >= (int)frozen->size() || (*frozen)[l].empty();
         DBuf<int> arp, aci;
         int annz = 0;
@@ -369,7 +415,9 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
                 h->lev.push_back(std::move(N));
             }
         }
-        if (last && L.A.n <= o.dense_max) {
+        if (two_grid && l == 1) {
+            build_ilut_level(L, o, s);
+        } else if (last && L.A.n <= o.dense_max) {
             L.dense = true;
             dense_inverse(L.A, L.inv, s);
         } else {
@@ -402,7 +450,7 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
                 cast_f64_f32(L.AT.v.get(), L.vt32.get(), L.AT.nnz, s);
             }
             if (!L.dense) {
-                build_transposed_sweeps(L.A, L.pos.get(), L.lu.get(), L.fwdT, L.bwdT, s);
+                build_transposed_sweeps(L.ilut_level ? L.fpat : L.A, L.pos.get(), L.lu.get(), L.fwdT, L.bwdT, s);
                 cast_sweep(L.fwdT, prec, s);
                 cast_sweep(L.bwdT, prec, s);
             }
@@ -592,6 +640,7 @@ struct VCycle {
             return;
         }
         if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 0, 0, s); return; }
+        if (Lv.ilut_level) { smooth(Lv, hrhs, ws(Lv.wy), g, false); return; }   // g = (L~ U~)^{-1} h
         const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
         T *res = ws(Lv.wres);
         for (int it = 0; it < k; ++it) {
@@ -633,6 +682,7 @@ struct VCycle {
         }
         Level &Lv = L(l);
         if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 1, 0, s); return; }
+        if (Lv.ilut_level) { smooth(Lv, hrhs, ws(Lv.wy), g, true); return; }    // g = (L~ U~)^{-T} h
         const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
         T *res = ws(Lv.wres);
         for (int it = 0; it < k; ++it) {
@@ -1069,6 +1119,9 @@ int amg_default_options(amg_options_t *o) {
     o->dot2 = -1;
     o->reserved0 = 0;
     o->seed = 0;
+    o->coarse_solver = AMG_COARSE_RECURSIVE;
+    o->reserved1 = 0;
+    o->ilut_tau = 1e-6;
     return AMG_OK;
 }
 
@@ -1081,7 +1134,8 @@ static void check_options(const amg_options_t &o) {
         (o.spmv_block != 0 && o.spmv_block != 64 && o.spmv_block != 128 && o.spmv_block != 256 &&
          o.spmv_block != 512) ||
         (o.spmv_unroll != 0 && o.spmv_unroll != 2 && o.spmv_unroll != 4 && o.spmv_unroll != 8) || o.dot2 < -1 ||
-        o.dot2 > 1)
+        o.dot2 > 1 || o.coarse_solver < 0 || o.coarse_solver > 1 || !(o.ilut_tau >= 0.0) ||
+        !std::isfinite(o.ilut_tau))
         fail(AMG_ERR_INVALID_ARG, "option out of range (restart <= 31, dense_max <= 4096, 2 <= max_levels <= 24)");
 }
 
@@ -1469,7 +1523,7 @@ int amg_get_pass_matrix(amg_handle_t *h, int32_t level, int32_t pass, int64_t *i
 int amg_get_colors(amg_handle_t *h, int32_t level, int32_t *out) {
     ABI_TRY
     Level &L = level_of(h, level);
-    if (!out || L.dense) fail(AMG_ERR_INVALID_ARG, "no smoother on this level");
+    if (!out || L.dense || L.ilut_level) fail(AMG_ERR_INVALID_ARG, "no ILU(0) factors on this level");
     CU(cudaMemcpy(out, L.label.get(), sizeof(int) * L.A.n, cudaMemcpyDeviceToHost));
     return AMG_OK;
     ABI_CATCH

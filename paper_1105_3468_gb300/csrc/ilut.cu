@@ -108,6 +108,16 @@ static void ilut_factor_host(int n, const int64_t *rp, const int32_t *ci, const 
     }
 }
 
+bool ilut_factor_host(int n, const int64_t *rp, const int32_t *ci, const double *val, double tau,
+                      std::vector<int64_t> &frp, std::vector<int32_t> &fci, std::vector<double> &fv) {
+    IlutHost F;
+    ilut_factor_host(n, rp, ci, val, tau, F);
+    frp.swap(F.rp);
+    fci.swap(F.ci);
+    fv.swap(F.v);
+    return !F.breakdown;
+}
+
 }  // namespace amg
 
 extern "C" int amg_ilut_host(int32_t n, const int64_t *row_ptr, const int32_t *col, const double *val, double tau,

@@ -158,6 +158,15 @@ void elimination_positions(int n, const int *label, int nlabels, int *pos, cudaS
 void ilu0_factor(const DCsr &A, const int *pos, DBuf<double> &lu, Sweep &fwd, Sweep &bwd,
                  cudaStream_t s);
 
+// Sweep schedules of factors already computed on the pattern of F (values lu
+// on F's layout; L part: pos(j) < pos(i), U part with the diagonal).
+void factor_sweeps(const DCsr &F, const int *pos, const double *lu, Sweep &fwd, Sweep &bwd, cudaStream_t s);
+
+// ILUT(tau) of a host CSR matrix (ilut.cu): rows of L~ (unit diagonal implied)
+// then U~, ascending columns.  Returns false on a zero or non-finite pivot.
+bool ilut_factor_host(int n, const int64_t *rp, const int32_t *ci, const double *val, double tau,
+                      std::vector<int64_t> &frp, std::vector<int32_t> &fci, std::vector<double> &fv);
+
 // Dense inverse (Gauss-Jordan with partial pivoting, FP64) of a CSR matrix.
 void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s);
 

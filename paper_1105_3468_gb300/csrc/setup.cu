@@ -830,6 +830,15 @@ void ilu0_factor(const DCsr &A, const int *pos, DBuf<double> &lu, Sweep &fwd, Sw
     build_sweep(A, pos, lu.get(), 0, 1, levb.get(), nb, bwd, s);
 }
 
+void factor_sweeps(const DCsr &F, const int *pos, const double *lu, Sweep &fwd, Sweep &bwd, cudaStream_t s) {
+    const int n = F.n;
+    DBuf<int> levf(n), levb(n);
+    const int nf = schedule_levels(F, pos, 1, levf.get(), s);
+    const int nb = schedule_levels(F, pos, 0, levb.get(), s);
+    build_sweep(F, pos, lu, 1, 0, levf.get(), nf, fwd, s);
+    build_sweep(F, pos, lu, 0, 1, levb.get(), nb, bwd, s);
+}
+
 __global__ void k_gather_vals(const double *src, const int *idx, double *dst, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[idx[i]];
 }

@@ -40,6 +40,7 @@ def test_host_only_calls(lib):
     o = pkg.amg_default_options()
     assert (o.passes, o.coarse_inner, o.restart, o.maxit, o.dense_max) == (2, 5, 30, 600, 4096)
     assert o.order_fine == pkg.AMG_ORDER_NATURAL and o.order_coarse == pkg.AMG_ORDER_COLOR
+    assert o.coarse_solver == pkg.AMG_COARSE_RECURSIVE and o.ilut_tau == 1e-6
     assert pkg.amg_status_string(pkg.AMG_ERR_NOT_CONVERGED) == "not converged"
     assert lib.amg_default_options(None) == pkg.AMG_ERR_INVALID_ARG
     out = C.c_void_p(123)
@@ -51,5 +52,5 @@ def test_host_only_calls(lib):
 
 def test_struct_sizes_match_header():
     from paper_1105_3468_gb300 import _lib
-    assert C.sizeof(_lib.AmgOptions) == 20 * 4 + 8
+    assert C.sizeof(_lib.AmgOptions) == 20 * 4 + 8 + 2 * 4 + 8
     assert C.sizeof(_lib.AmgStats) == 4 * 4 + 3 * 8 + 2 * 4 + 2 * 8
