@@ -327,6 +327,9 @@ def main():
     ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
     ap.add_argument("--dense-max", type=int, default=None,
                     help="largest level (rows) solved exactly by its dense inverse")
+    ap.add_argument("--coarse-solver", type=int, default=None, choices=[0, 1],
+                    help="0 recursive coarse solve (default), 1 two-grid with an ILUT-factored coarse level")
+    ap.add_argument("--ilut-tau", type=float, default=None, help="drop tolerance of --coarse-solver 1")
     ap.add_argument("--deep-block-max", type=int, default=None,
                     help="levels >= 2 with at most this many rows run their V-cycle in one thread block")
     args = ap.parse_args()
@@ -359,7 +362,7 @@ def main():
     torch.cuda.synchronize()
     vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
     opts = dict(sopts, maxit=maxit)
-    for k in ("persistent", "orthog", "deep_block_max", "dense_max"):
+    for k in ("persistent", "orthog", "deep_block_max", "dense_max", "coarse_solver", "ilut_tau"):
         if getattr(args, k) is not None:
             opts[k] = getattr(args, k)
 
