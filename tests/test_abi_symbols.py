@@ -54,3 +54,17 @@ def test_struct_sizes_match_header():
     from paper_1105_3468_gb300 import _lib
     assert C.sizeof(_lib.AmgOptions) == 20 * 4 + 8 + 2 * 4 + 8
     assert C.sizeof(_lib.AmgStats) == 4 * 4 + 3 * 8 + 2 * 4 + 2 * 8
+
+
+def test_setup_rejects_bad_options_before_any_device_call(lib):
+    """amg_setup validates its options first (no GPU needed to see that)."""
+    import paper_1105_3468_gb300 as pkg
+    from paper_1105_3468_gb300 import _lib
+    A = _lib.AmgCsr()
+    out = C.c_void_p()
+    for field, value in (("coarse_solver", 2), ("ilut_tau", -1.0), ("ilut_tau", float("nan")),
+                         ("ilut_tau", float("inf")), ("dense_max", 4097), ("persistent", 5), ("passes", 0)):
+        o = pkg.amg_default_options()
+        setattr(o, field, value)
+        assert lib.amg_setup(C.byref(A), C.byref(o), None, C.byref(out)) == pkg.AMG_ERR_INVALID_ARG, field
+        assert not out.value
