@@ -198,8 +198,8 @@ int amg_default_options(amg_options_t *opt);
  * copies and, if requested, the transposed structures.  A's arrays are host
  * or device; they are copied.  `stream` is a cudaStream_t (NULL allowed).
  * Errors: AMG_ERR_INVALID_ARG (bad CSR: unsorted or out-of-range columns,
- * missing diagonal, nnz >= 2^31; bad option), AMG_ERR_BREAKDOWN (zero ILU
- * or dense pivot), AMG_ERR_LIMIT (matching/colouring rounds or a coarse row
+ * missing diagonal, nnz >= 2^31; bad option), AMG_ERR_BREAKDOWN (zero ILU(0),
+ * ILUT or dense pivot), AMG_ERR_LIMIT (matching/colouring rounds or a coarse row
  * over its capacity), AMG_ERR_OOM, AMG_ERR_CUDA.  On error *out is NULL. */
 int amg_setup(const amg_csr_t *A, const amg_options_t *opt, void *stream,
               amg_handle_t **out);
