@@ -341,7 +341,9 @@ int amg_get_colors(amg_handle_t *h, int32_t level, int32_t *out);
 
 /* FP64 ILU(0) factors of level l on that level's CSR layout: L entries
  * (unit diagonal implied) before the row in the elimination order, U
- * entries (with the diagonal) after.  out: host [nnz]. */
+ * entries (with the diagonal) after.  out: host [nnz].  AMG_ERR_INVALID_ARG
+ * on the dense level and on the ILUT level of AMG_COARSE_ILUT (its factors
+ * have their own pattern: amg_ilut_host computes the same factors). */
 int amg_get_ilu(amg_handle_t *h, int32_t level, double *out);
 
 /* ------------------------------------------------------------ profiling */

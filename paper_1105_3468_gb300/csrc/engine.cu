@@ -1523,7 +1523,7 @@ int amg_get_pass_matrix(amg_handle_t *h, int32_t level, int32_t pass, int64_t *i
 int amg_get_colors(amg_handle_t *h, int32_t level, int32_t *out) {
     ABI_TRY
     Level &L = level_of(h, level);
-    if (!out || L.dense || L.ilut_level) fail(AMG_ERR_INVALID_ARG, "no ILU(0) factors on this level");
+    if (!out || L.dense) fail(AMG_ERR_INVALID_ARG, "no elimination order on this level");
     CU(cudaMemcpy(out, L.label.get(), sizeof(int) * L.A.n, cudaMemcpyDeviceToHost));
     return AMG_OK;
     ABI_CATCH
@@ -1532,7 +1532,8 @@ int amg_get_colors(amg_handle_t *h, int32_t level, int32_t *out) {
 int amg_get_ilu(amg_handle_t *h, int32_t level, double *out) {
     ABI_TRY
     Level &L = level_of(h, level);
-    if (!out || L.dense) fail(AMG_ERR_INVALID_ARG, "no smoother on this level");
+    if (!out || L.dense || L.ilut_level)   // ILUT factors have their own pattern
+        fail(AMG_ERR_INVALID_ARG, "no ILU(0) factors on this level");
     CU(cudaMemcpy(out, L.lu.get(), sizeof(double) * L.A.nnz, cudaMemcpyDeviceToHost));
     return AMG_OK;
     ABI_CATCH
