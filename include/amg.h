@@ -12,8 +12,8 @@
  *     Galerkin coarse matrix A_c = P^T A P (eq. (3) of Section 2 and its
  *     entrywise form), ILU(0) smoother S = L0 U0 (Algorithm 1, setup);
  *   - preconditioner B~ = (S^{-1} + M~^{-1} - M~^{-1} A S^{-1})^{-1} without
- *     post-smoothing, M~ = P A~_c P^T (eq. (5), Algorithm 1 "SOLVE B~q=z"
- *     and "SOLVE M~g=h");
+ *     post-smoothing, M~ = P A~_c P^T (eq. (5), Algorithm 1's preconditioner and coarse-solve
+ *     applications);
  *   - Krylov accelerator: GMRES with Givens rotations (Algorithm 1), here
  *     the flexible right-preconditioned variant FGMRES(m).
  * Readings where the paper is silent (matching rule and tie-breaks, the
@@ -192,7 +192,7 @@ const char *amg_last_error(void);
 int amg_default_options(amg_options_t *opt);
 
 /* --------------------------------------------------------------- setup */
-/* Builds the hierarchy for A (Algorithm 1, SETUP PHASE): per level the
+/* Builds the hierarchy for A (Algorithm 1, setup): per level the
  * matching passes, aggregates, Galerkin products, the ILU(0) factors in the
  * chosen order, and the dense inverse of the last level; then the FP32/BF16
  * copies and, if requested, the transposed structures.  A's arrays are host
@@ -239,7 +239,7 @@ int amg_ilut_host(int32_t n, const int64_t *row_ptr, const int32_t *col, const d
 
 /* --------------------------------------------------------------- solve */
 /* Solves A x = b by FGMRES(restart) preconditioned with B~ (Algorithm 1,
- * PRECONDITIONED GMRES ITERATION), stopping when the true relative residual
+ * Krylov iteration), stopping when the true relative residual
  * ||b - A x|| / ||b|| <= tol (Section 3 stopping rule).  b: host or device
  * [n]; x: host or device [n], read as the initial guess, written with the
  * result.  stats may be NULL.  Returns AMG_ERR_NOT_CONVERGED when maxit is
@@ -287,26 +287,32 @@ int amg_get_history(amg_handle_t *h, double *out, int32_t cap, int32_t *len);
 
 /* q = B~^{-1} z (transpose = 0) or B~^{-T} z (transpose = 1) at level 0, in
  * the handle's V-cycle precision with FP64 input and output (Algorithm 1,
- * SOLVE B~q = z).  z, q: device [n]. */
+ * preconditioner application).  z, q: device [n]. */
 int amg_precond_apply(amg_handle_t *h, const double *z, double *q, int32_t transpose);
 
 /* y = A x in FP64 for a CSR given on the device (row_ptr int64).  x, y:
- * device [n].  Stream-ordered on `stream`; does not synchronise. */
+ * device [n].  Synchronises `stream`.  Errors: AMG_ERR_INVALID_ARG for a
+ * null pointer, nnz >= 2^31, row pointers that are not a non-decreasing
+ * sequence from 0 to nnz, or columns outside [0, n) (no out-of-range entry
+ * is ever used as an index: y is then unspecified); AMG_ERR_CUDA. */
 int amg_spmv(const amg_csr_t *A, const double *x, double *y, void *stream);
 
 /* y = A x like amg_spmv, for callers that must not let the library allocate
- * device memory (for example code capturing a CUDA graph on `stream`, or
- * code that owns a fixed memory budget): the int32 row-pointer copy that
- * amg_spmv allocates per call lives instead in a fixed file-scope device
- * array of AMG_NOALLOC_MAX_ROWS + 1 entries plus a status word (16 MiB +
- * 512 B), held by every GPU that loads the library until the process exits.
- * The paper has no counterpart: this is an interface variant only.
- * Pointers as in amg_spmv (device).  The first call on a device looks up the
- * array's address with that device current; make that first call before any
- * stream capture.  Every call shares the array, so calls that overlap on the
- * GPU race: serialise them on one stream.  Synchronises `stream`.  Errors:
- * AMG_ERR_INVALID_ARG for n > AMG_NOALLOC_MAX_ROWS, nnz >= 2^31, null
- * pointers or invalid row pointers; AMG_ERR_CUDA. */
+ * device memory: a process whose own caching allocator has reserved the free
+ * device memory up front (a library cudaMalloc would fail or eat into its
+ * budget), or a loop that must not stall the device (cudaFree synchronises
+ * the whole device).  The int32 row-pointer copy that amg_spmv allocates per
+ * call lives instead in a fixed file-scope device array of
+ * AMG_NOALLOC_MAX_ROWS + 1 entries plus a status word (16 MiB + 512 B), held
+ * by every GPU that loads the library until the process exits.  The paper
+ * has no counterpart: this is an interface variant only.  Pointers as in
+ * amg_spmv (device).  The first call on a device looks up the array's
+ * address with that device current.  Every call shares the array, so calls
+ * that overlap on the GPU race: serialise them on one stream.  Synchronises
+ * `stream`.  Errors: AMG_ERR_INVALID_ARG for n > AMG_NOALLOC_MAX_ROWS,
+ * nnz >= 2^31, null pointers, row pointers that are not a non-decreasing
+ * sequence from 0 to nnz, or columns outside [0, n) (no out-of-range entry
+ * is ever used as an index); AMG_ERR_CUDA. */
 #define AMG_NOALLOC_MAX_ROWS 4194304
 int amg_spmv_noalloc(const amg_csr_t *A, const double *x, double *y, void *stream);
 

@@ -422,7 +422,7 @@ class Hierarchy:
         return out
 
     def precond(self, z, transpose=False, level: int = 0):
-        """q = B~^{-1} z (Algorithm 1, SOLVE B~q = z) at a level, or its transpose."""
+        """q = B~^{-1} z (Algorithm 1, the preconditioner application) at a level, or its transpose."""
         out = np.zeros(self.levels[level]["n"])
         lib().or_precond_level(self._h, level, _f64(z), out, int(transpose))
         return out

@@ -477,7 +477,7 @@ static void colour_order(int n, const int32_t *color, int32_t *perm, int32_t *po
 }
 
 /* ------------------------------------------------------------------ */
-/* O5b. ILU(0) (Algorithm 1, "Setup smoother: S = L0 U0 = ILU0(A)")     */
+/* O5b. ILU(0) (Algorithm 1, smoother setup: zero-fill incomplete LU)     */
 /* in the colour-major elimination order: the IKJ variant restricted    */
 /* to the pattern of A.  For each row i in order, for each k with        */
 /* pos(k) < pos(i) stored in row i, in increasing pos(k):                */
@@ -788,23 +788,16 @@ static int dense_inverse(int n, const double *a, double *inv)
 }
 
 /* x = A^{-1} b (transpose = 0) or A^{-T} b (transpose = 1) from the     */
-/* inverse.  Summation order (the paper prescribes none): the terms of   */
-/* x_i form 32 interleaved partial sums, s_r over j = r, r + 32, ... in  */
-/* ascending j with fused multiply-adds, which are then added by         */
-/* halving, s_r + s_{r+16}, then + the same at 8, 4, 2, 1.               */
+/* inverse: x_i = sum_j inv_ij b_j (inv_ji for the transpose), one        */
+/* accumulator per row in ascending j, each term added with a fused       */
+/* multiply-add (solve-phase rounding).                                   */
 static void dense_solve(int n, const double *inv, const double *b, double *x, int transpose)
 {
     for (int i = 0; i < n; ++i) {
-        double t[32];
-        for (int r = 0; r < 32; ++r) {
-            double s = 0.0;
-            for (int j = r; j < n; j += 32)
-                s = fma(transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j], b[j], s);
-            t[r] = s;
-        }
-        for (int off = 16; off >= 1; off >>= 1)
-            for (int r = 0; r < off; ++r) t[r] = t[r] + t[r + off];
-        x[i] = t[0];
+        double s = 0.0;
+        for (int j = 0; j < n; ++j)
+            s = fma(transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j], b[j], s);
+        x[i] = s;
     }
 }
 
@@ -1048,7 +1041,7 @@ void or_hier_lu(const or_hier_t *H, int l, double *out)
 }
 
 /* ------------------------------------------------------------------ */
-/* O6. Preconditioner.  Algorithm 1 (SOLVE B~q = z) computes            */
+/* O6. Preconditioner.  Algorithm 1's preconditioner application does   */
 /*   S t = z; M~ f = z; M~ q' = A t; q = t + f - q'                      */
 /* with M~^{-1} = P A~_c^{-1} P^T linear, so q = t + M~^{-1}(z - A t):   */
 /* one coarse solve of the restricted residual (eq. (5), inexact M~).    */

@@ -1,9 +1,9 @@
 // engine.cu -- the C ABI of libamg_gb (include/amg.h): the handle, the
-// setup pipeline (Algorithm 1, SETUP PHASE, applied level by level), the
-// recursive preconditioner (Algorithm 1, SOLVE B~q = z and SOLVE M~g = h,
+// setup pipeline (Algorithm 1, setup, applied level by level), the
+// recursive preconditioner (Algorithm 1, the two-grid and coarse-solve applications,
 // with the inexact coarse solve read as Richardson steps preconditioned by
 // the coarse level's own two-grid construction), and right-preconditioned
-// FGMRES(m) (Algorithm 1, PRECONDITIONED GMRES ITERATION, flexible form).
+// FGMRES(m) (Algorithm 1, Krylov iteration, flexible form).
 #include "../../include/amg.h"
 #include "solve.cuh"
 #include <type_traits>
@@ -130,7 +130,7 @@ __global__ void k_rp64_to_32(int n, int64_t nnz, const int64_t *rp64, int *rp32,
         if (i == n && v != nnz) ok = false;
         if (i < n && rp64[i + 1] < v) ok = false;
         if (!ok) atomicAdd(bad, 1);
-        rp32[i] = (int)v;
+        rp32[i] = (int)(v < 0 ? 0 : (v > nnz ? nnz : v));   // a bad entry never becomes an index
     }
 }
 
@@ -1405,8 +1405,11 @@ int amg_spmv(const amg_csr_t *A, const double *x, double *y, void *stream) {
     CU(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
     k_rp64_to_32<<<grid_for((size_t)A->n + 1, 256), 256, 0, s>>>(A->n, A->nnz, A->row_ptr, rp32.get(), bad.get());
     CU_LAUNCH("k_rp64_to_32"); count_launch();
-    spmv_f64(A->n, (int)A->nnz, rp32.get(), A->col, A->val, x, y, s);
+    spmv_f64_checked(A->n, (int)A->nnz, rp32.get(), A->col, A->val, x, y, bad.get(), s);
+    int hbad = 0;
+    CU(cudaMemcpyAsync(&hbad, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (hbad) fail(AMG_ERR_INVALID_ARG, "amg_spmv: row pointers not a valid sequence from 0 to nnz, or columns out of range");
     return AMG_OK;
     ABI_CATCH
 }

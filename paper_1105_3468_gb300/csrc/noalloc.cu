@@ -3,12 +3,14 @@
 //
 // amg_spmv converts the caller's int64 row pointers to an int32 copy in a
 // temporary device buffer it allocates per call.  Some callers cannot let a
-// library call cudaMalloc/cudaFree: code that runs while a CUDA graph is
-// being captured on its stream, code that holds a fixed device-memory budget
-// carved out in advance, or code running between the steps of another
-// library that owns the allocator.  For them this entry point keeps that
-// buffer in a file-scope device array of fixed size instead, so a call
-// allocates nothing.
+// library call cudaMalloc/cudaFree:
+//   * a serving or training process whose own caching allocator has already
+//     reserved the free device memory at start-up: a cudaMalloc from a
+//     library then fails, or takes memory the process's budget counts on;
+//   * a latency-bound loop that must not stall the whole device: cudaFree
+//     synchronises the device, not just the caller's stream.
+// For them this entry point keeps that buffer in a file-scope device array
+// of fixed size instead, so a call allocates nothing.
 //
 // Limits and sharing:
 //   * At most AMG_NOALLOC_MAX_ROWS rows (the array holds n + 1 int32 row
@@ -20,6 +22,10 @@
 //     stream, or serialise them.
 //   * The status word is cleared at the start of each call; the row-pointer
 //     copy is fully rewritten by each call.
+//   * Invalid input cannot make the kernels read outside the caller's
+//     buffers: row pointers are clamped to [0, nnz] when they are narrowed,
+//     and a column outside [0, n) is skipped and counted in the status word,
+//     which the call reads back after synchronising `stream`.
 //   * The array's device address is looked up once per device, the first
 //     time the entry point runs with that device current.
 #include "../../include/amg.h"
@@ -64,7 +70,7 @@ __global__ void k_noalloc_rp32(int n, int64_t nnz, const int64_t *rp64, int *scr
         if (i == n && v != nnz) ok = false;
         if (i < n && rp64[i + 1] < v) ok = false;
         if (!ok) atomicAdd(scratch + NOALLOC_STATUS, 1);
-        scratch[i] = (int)v;
+        scratch[i] = (int)(v < 0 ? 0 : (v > nnz ? nnz : v));   // a bad entry never becomes an index
     }
 }
 
@@ -86,11 +92,13 @@ extern "C" int amg_spmv_noalloc(const amg_csr_t *A, const double *x, double *y, 
         k_noalloc_rp32<<<grid_for((size_t)A->n + 1, 256), 256, 0, s>>>(A->n, A->nnz, A->row_ptr, scratch);
         CU_LAUNCH("k_noalloc_rp32");
         count_launch();
-        spmv_f64(A->n, (int)A->nnz, scratch, A->col, A->val, x, y, s);
+        spmv_f64_checked(A->n, (int)A->nnz, scratch, A->col, A->val, x, y, scratch + NOALLOC_STATUS, s);
         int bad = 0;
         CU(cudaMemcpyAsync(&bad, scratch + NOALLOC_STATUS, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        if (bad) fail(AMG_ERR_INVALID_ARG, "amg_spmv_noalloc: row pointers are not a valid sequence from 0 to nnz");
+        if (bad)
+            fail(AMG_ERR_INVALID_ARG,
+                 "amg_spmv_noalloc: row pointers not a valid sequence from 0 to nnz, or columns out of range");
         return AMG_OK;
     } catch (const Error &e) {
         amg_noalloc_set_error(e.msg.c_str());

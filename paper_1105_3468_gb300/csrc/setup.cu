@@ -1,5 +1,5 @@
 // setup.cu -- GPU setup phase of the matching-aggregation AMG hierarchy
-// (Algorithm 1, SETUP PHASE of the paper): heavy-edge matching, aggregates,
+// (Algorithm 1, setup): heavy-edge matching, aggregates,
 // Galerkin products P^T A P, colourings, ILU(0) factors with their sweep
 // schedules, the dense inverse of the last level, precision casts, and the
 // finite-volume assembly of eq. (2).
@@ -657,8 +657,8 @@ static void build_sweep(const DCsr &A, const int *pos, const double *lu, int fwd
 }
 
 // ------------------------------------------------------------------ ILU(0)
-// IKJ ILU(0) on the pattern of A in the elimination order pos (Algorithm 1:
-// S = L0 U0 = ILU0(A)): for each stored k of row i with pos(k) < pos(i), in
+// IKJ ILU(0) on the pattern of A in the elimination order pos (Algorithm 1,
+// smoother setup): for each stored k of row i with pos(k) < pos(i), in
 // increasing pos(k): a_ik /= a_kk, then a_ij -= a_ik a_kj for every stored
 // (k, j) with pos(j) > pos(k) whose (i, j) is stored.  Rows of one schedule
 // level only read rows of earlier levels, so a level runs in parallel.

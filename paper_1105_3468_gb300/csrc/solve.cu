@@ -108,6 +108,48 @@ void spmv_t(int n, int nnz, const int *rp, const int *ci, const VT *v, const XT 
 void spmv_f64(int n, int nnz, const int *rp, const int *ci, const double *v, const double *x, double *y, cudaStream_t s) {
     spmv_t<double, double, double, double>(n, nnz, rp, ci, v, x, nullptr, y, 0, s);
 }
+// y = A x for a caller's CSR whose indices have not been validated: a row
+// reads only e in [rp[i], rp[i+1]) (the row pointers were clamped to
+// [0, nnz] when they were narrowed), and a column outside [0, n) is skipped
+// and counted in *bad instead of being used as an index into x.
+template <int G>
+__global__ void __launch_bounds__(256) k_spmv_checked(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                      const double *__restrict__ v, const double *__restrict__ x,
+                                                      double *__restrict__ y, int *bad) {
+    const int lane = threadIdx.x % G;
+    const int rows_per_block = blockDim.x / G;
+    for (int r0 = blockIdx.x * rows_per_block; r0 < n; r0 += gridDim.x * rows_per_block) {
+        const int i = r0 + threadIdx.x / G;
+        double acc = 0.0;
+        int nbad = 0;
+        if (i < n) {
+            const int e1 = rp[i + 1];
+            for (int e = rp[i] + lane; e < e1; e += G) {
+                const int c = ci[e];
+                if ((unsigned)c < (unsigned)n) acc += v[e] * x[c];
+                else ++nbad;
+            }
+        }
+        if (nbad) atomicAdd(bad, nbad);
+#pragma unroll
+        for (int off = G / 2; off; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, G);
+        if (lane == 0 && i < n) y[i] = acc;
+    }
+}
+
+void spmv_f64_checked(int n, int nnz, const int *rp, const int *ci, const double *v, const double *x, double *y,
+                      int *bad, cudaStream_t s) {
+    if (n <= 0) return;
+    const int avg = nnz / n;
+    if (avg <= 6) {
+        k_spmv_checked<4><<<grid_for((size_t)n * 4, 256), 256, 0, s>>>(n, rp, ci, v, x, y, bad);
+    } else if (avg <= 12) {
+        k_spmv_checked<8><<<grid_for((size_t)n * 8, 256), 256, 0, s>>>(n, rp, ci, v, x, y, bad);
+    } else {
+        k_spmv_checked<16><<<grid_for((size_t)n * 16, 256), 256, 0, s>>>(n, rp, ci, v, x, y, bad);
+    }
+    CU_LAUNCH("k_spmv_checked"); count_launch();
+}
 void spmv_f64_xf32(int n, int nnz, const int *rp, const int *ci, const double *v, const float *x, double *y, cudaStream_t s) {
     spmv_t<double, float, double, double>(n, nnz, rp, ci, v, x, nullptr, y, 0, s);
 }

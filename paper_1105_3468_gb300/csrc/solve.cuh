@@ -42,6 +42,8 @@ struct SweepView {
 };
 
 void spmv_f64(int n, int nnz, const int *rp, const int *ci, const double *v, const double *x, double *y, cudaStream_t s);
+void spmv_f64_checked(int n, int nnz, const int *rp, const int *ci, const double *v, const double *x, double *y,
+                      int *bad, cudaStream_t s);
 void spmv_f64_xf32(int n, int nnz, const int *rp, const int *ci, const double *v, const float *x, double *y, cudaStream_t s);
 void residual_f64(int n, int nnz, const int *rp, const int *ci, const double *v, const double *x, const double *b,
                   double *r, cudaStream_t s);

@@ -1,6 +1,6 @@
 """Pins of the oracle's smoother, preconditioner and Krylov solver.
 
-Colouring / ILU(0) (Algorithm 1: S = L0 U0 = ILU0(A); orderings of
+Colouring / ILU(0) (Algorithm 1, smoother setup; orderings of
 Section 3):
 * colourings are proper and greedy (every vertex of colour c > 0 has a
   higher-priority neighbour of each colour below c); first-fit colouring of
@@ -11,7 +11,7 @@ Section 3):
   a breakdown;
 * for a symmetric M-matrix the ILU iteration converges (Theorem of Meijerink
   and van der Vorst quoted in Section 2.1): rho(I - S^{-1}A) < 1.
-Preconditioner (eq. (5), Algorithm 1 SOLVE B~q = z):
+Preconditioner (eq. (5), Algorithm 1's preconditioner application):
 * equals the paper's three-solve form t + f - q';
 * with an exact coarse solve, (I - M^{-1}A) P = 0 (Theorem 1);
 * the Richardson coarse solve equals sum_{k<m} (I - B^{-1}A)^k B^{-1};

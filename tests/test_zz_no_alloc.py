@@ -1,6 +1,7 @@
 """amg_spmv_noalloc: the SpMV entry point for callers that cannot let the
-library allocate device memory (graph capture in progress on their stream, a
-fixed memory budget).  Its scratch (the int32 row-pointer copy) lives in a
+library allocate device memory (a process whose own allocator has reserved
+the free device memory, or a loop that must not be stalled by the device-wide
+synchronisation of cudaFree).  Its scratch (the int32 row-pointer copy) lives in a
 fixed device array shared by every call.  This file is collected last so a
 failure here stops a -x run only after every other test has run; it also
 passes alone in a fresh process (the first call looks the array up)."""
@@ -55,3 +56,31 @@ def test_noalloc_rejects_oversized(env):
         amg.amg_spmv_noalloc(A, x, x)
     assert e.value.status == amg.AMG_ERR_INVALID_ARG
     assert "AMG_NOALLOC_MAX_ROWS" in str(e.value)
+
+
+def test_invalid_indices_rejected_without_out_of_range_reads(env):
+    """A row pointer beyond nnz or a column outside [0, n) is reported as
+    AMG_ERR_INVALID_ARG by amg_spmv and amg_spmv_noalloc.  The kernels clamp
+    the row pointers to [0, nnz] and skip such columns, so no entry is used as
+    an index outside the caller's buffers; the next valid call is exact."""
+    amg, torch = env
+    A = W.rgg_matrix(3_001, 9, seed=23)
+    x = torch.tensor(np.random.default_rng(12).standard_normal(A.n), device="cuda")
+    y_ref = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    good = amg.CsrDevice.from_host(A)
+    amg.amg_spmv(good, x, y_ref)
+    bad_rp = amg.CsrDevice.from_host(A)
+    bad_rp.row_ptr[A.n // 2] = A.nnz + 100
+    bad_col = amg.CsrDevice.from_host(A)
+    bad_col.col[A.nnz // 3] = A.n + 5
+    for call in (amg.amg_spmv, amg.amg_spmv_noalloc):
+        for bad in (bad_rp, bad_col):
+            y = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+            with pytest.raises(amg.AmgError) as e:
+                call(bad, x, y)
+            assert e.value.status == amg.AMG_ERR_INVALID_ARG
+        y = torch.full((A.n,), float("nan"), dtype=torch.float64, device="cuda")
+        call(good, x, y)
+        torch.cuda.synchronize()
+        ref = y_ref.cpu().numpy()
+        assert np.allclose(y.cpu().numpy(), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
