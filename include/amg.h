@@ -76,6 +76,10 @@ extern "C" {
 #define AMG_COLOR_HASH_JP 0     /* priority (mix64(i ^ (seed + 0x9e3779b97f4a7c15)), i) */
 #define AMG_COLOR_FIRST_FIT 1   /* priority -i (first fit in index order)  */
 
+/* Edge weight of the heavy-edge matching (amg_options_t.match_weight). */
+#define AMG_MATCH_PLAIN 0       /* w_uv = (|a_uv| + |a_vu|)/2              */
+#define AMG_MATCH_SCALED 1      /* the same divided by sqrt(|a_uu| |a_vv|) */
+
 /* Coarse solve of level 1 (amg_options_t.coarse_solver). */
 #define AMG_COARSE_RECURSIVE 0  /* coarse_inner Richardson steps, each
                                    preconditioned by the same two-grid
@@ -104,7 +108,9 @@ typedef struct {
      * passes (aggregates of at most 2^passes points; Section 2 aggregation
      * by graph matching).  Matching rule: greedy maximal matching in
      * decreasing key order, key = (w_uv, mix64(((u<<32)|v) ^ seed), u, v),
-     * w_uv = (|a_uv| + |a_vu|)/2, u < v, edges with w > 0. */
+     * u < v, edges with w > 0; w_uv = (|a_uv| + |a_vu|)/2 divided by
+     * sqrt(|a_uu| |a_vv|) (match_weight = AMG_MATCH_SCALED), or not divided
+     * (AMG_MATCH_PLAIN). */
     int32_t passes;           /* default 2                                 */
     int32_t coarse_inner;     /* Richardson steps solving level 1: 5       */
     int32_t deep_inner;       /* Richardson steps on levels >= 2: 1        */
@@ -160,7 +166,12 @@ typedef struct {
                                  Rump-Oishi 2005), independent of the
                                  reduction order: 1 on, 0 plain FMA sums,
                                  -1 = on with the FP64 V-cycle only: -1    */
-    int32_t reserved0;        /* 0                                         */
+    int32_t match_weight;     /* AMG_MATCH_SCALED: the coupling measured
+                                 against its endpoints' diagonals, so a
+                                 vertex left unmatched on one level is not
+                                 outweighed forever by its growing
+                                 neighbours (default); AMG_MATCH_PLAIN:
+                                 the coupling alone                        */
     uint64_t seed;            /* tie-break seed, default 0                 */
     int32_t coarse_solver;    /* AMG_COARSE_RECURSIVE (default) or
                                  AMG_COARSE_ILUT                           */
@@ -396,6 +407,21 @@ int amg_fv_grad_logk(int32_t dim, int32_t nx, int32_t ny, int32_t nz,
                      const double *kx, const double *ky, const double *kz,
                      const double *lambda, const double *x,
                      double *gx, double *gy, double *gz, void *stream);
+
+/* The same assembly for an isotropic conductivity given by its logarithm:
+ * kappa = exp(logk) per cell is computed on the device into `kappa` (device
+ * [n], reused by amg_fv_grad_logk_iso), then eq. (2) is assembled with
+ * kx = ky = kz = kappa.  Other arguments and errors as amg_fv_assemble. */
+int amg_fv_assemble_logk(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *logk, double *kappa,
+                         const double *fx, const double *fy, const double *fz, const double *f,
+                         int64_t *row_ptr, int32_t *col, double *val, double *b, int64_t *nnz_out,
+                         void *stream);
+
+/* dL/dlog kappa per cell for an isotropic conductivity (kx = ky = kz =
+ * kappa): the derivative of amg_fv_grad_logk summed over the axes in the
+ * order (x + y) + z, in one kernel.  All pointers device [n]; g is written. */
+int amg_fv_grad_logk_iso(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *kappa,
+                         const double *lambda, const double *x, double *g, void *stream);
 
 /* Gradient of a loss with respect to the stored values of A for A x = b:
  * grad_val[k] = -lambda[row_k] * x[col_k] with lambda = A^{-T} dL/dx (the

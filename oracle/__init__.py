@@ -70,7 +70,9 @@ def lib():
             L.or_edge_hash.restype = C.c_uint64
             L.or_edge_hash.argtypes = [C.c_int, C.c_int, C.c_uint64]
             L.or_match.restype = C.c_int64
-            L.or_match.argtypes = [C.c_int, i64p, i32p, f64p, C.c_uint64, i32p]
+            L.or_match.argtypes = [C.c_int, i64p, i32p, f64p, C.c_uint64, C.c_int, i32p]
+            L.or_edge_key_weight.restype = C.c_double
+            L.or_edge_key_weight.argtypes = [i64p, i32p, f64p, C.c_int, C.c_int, C.c_int]
             L.or_aggregate.restype = C.c_int
             L.or_aggregate.argtypes = [C.c_int, i32p, i32p]
             L.or_galerkin.restype = C.c_int64
@@ -218,16 +220,26 @@ def edge_weight(A, u, v) -> float:
     return float(lib().or_edge_weight(A.row_ptr, A.col, A.val, u, v))
 
 
+def edge_key_weight(A, u, v, scaled: int = 1) -> float:
+    """Edge weight in the matching key (O2): plain, or divided by the
+    geometric mean of the two endpoints' diagonal magnitudes."""
+    A = as_csr(A)
+    return float(lib().or_edge_key_weight(A.row_ptr, A.col, A.val, u, v, scaled))
+
+
 def edge_hash(u, v, seed=0) -> int:
     return int(lib().or_edge_hash(u, v, seed))
 
 
 # ---------------------------------------------------------------- O2-O4
-def match(A, seed: int = 0):
+MATCH_PLAIN, MATCH_SCALED = 0, 1
+
+
+def match(A, seed: int = 0, weight: int = MATCH_SCALED):
     """Greedy heavy-edge matching (Section 2 aggregation by matching)."""
     A = as_csr(A)
     mate = np.zeros(A.n, np.int32)
-    lib().or_match(A.n, A.row_ptr, A.col, A.val, seed, mate)
+    lib().or_match(A.n, A.row_ptr, A.col, A.val, seed, weight, mate)
     return mate
 
 
@@ -333,6 +345,7 @@ class Options(NamedTuple):
     coarse_solver: int = COARSE_RECURSIVE   # COARSE_ILUT: two-grid, ILUT on level 1 (Section 2)
     ilut_tau: float = 1e-6    # drop tolerance of the ILUT two-grid (the paper's choice)
     seed: int = 0
+    match_weight: int = 1     # MATCH_SCALED (default) or MATCH_PLAIN edge weights
 
 
 class Hierarchy:
@@ -346,7 +359,7 @@ class Hierarchy:
         st = C.c_int(0)
         o = np.array([opts.passes, opts.coarse_inner, opts.deep_inner, opts.dense_max,
                       opts.max_levels, opts.order_fine, opts.order_coarse, opts.coloring,
-                      opts.coarse_solver], np.int32)
+                      opts.coarse_solver, opts.match_weight], np.int32)
         self._h = lib().or_setup(self.A.n, self.A.row_ptr, self.A.col, self.A.val, o,
                                  float(opts.ilut_tau), opts.seed, C.byref(st))
         self.status = st.value

@@ -291,11 +291,18 @@ static void sym_adjacency(int n, const int64_t *rp, const int32_t *ci,
 
 /* ------------------------------------------------------------------ */
 /* O2. Heavy-edge matching (one pass).  The paper forms aggregates from */
-/* a graph partition of G(A) (Section 2, "Aggregation based on graph    */
-/* matching"); the deterministic variant used here pairs vertices by a  */
+/* a graph partition of G(A) (Section 2, aggregation based on graph     */
+/* matching); the deterministic variant used here pairs vertices by a   */
 /* greedy maximal matching in decreasing edge-key order:                */
 /*   edge {u,v}, u<v, exists iff a_uv or a_vu is stored, with weight    */
 /*   w = (|a_uv| + |a_vu|) * 0.5 (missing entry = 0), kept iff w > 0;   */
+/*   scaled weight (scaled = 1): w / sqrt(|a_uu| |a_vv|), the strength  */
+/*   of connection of smoothed aggregation (Vanek, Mandel, Brezina,     */
+/*   Computing 56, 1996) measured on the symmetrised coupling (reading: */
+/*   the paper's partitioner keeps parts of equal size; unscaled        */
+/*   weights grow with the aggregates, so a vertex left single on one   */
+/*   level is outweighed by its neighbours on every later one and       */
+/*   coarsening stalls);                                                */
 /*   key = (w, mix64(((u<<32)|v) ^ seed), u, v), larger key first.      */
 /* mate[u] = partner or -1.  Returns the number of pairs or -errno.     */
 /* ------------------------------------------------------------------ */
@@ -321,6 +328,26 @@ double or_edge_weight(const int64_t *rp, const int32_t *ci, const double *v, int
     return (a1 + a2) * 0.5;
 }
 
+static double diag_abs(const int64_t *rp, const int32_t *ci, const double *v, int u)
+{
+    int64_t e = find_in_row(rp, ci, u, u);
+    return e >= 0 ? fabs(v[e]) : 0.0;
+}
+
+/* Weight of edge {u, w} in the matching key: plain, or divided by the  */
+/* geometric mean of its endpoints' diagonal magnitudes, sqrt(|a_uu|    */
+/* |a_ww|) with the product rounded first (a zero diagonal makes the    */
+/* quotient +inf, an ordinary key value).                               */
+double or_edge_key_weight(const int64_t *rp, const int32_t *ci, const double *v, int u, int w, int scaled)
+{
+    double x = or_edge_weight(rp, ci, v, u, w);
+    if (scaled && x > 0.0) {
+        double du = diag_abs(rp, ci, v, u), dw = diag_abs(rp, ci, v, w);
+        x = x / sqrt(du * dw);
+    }
+    return x;
+}
+
 uint64_t or_edge_hash(int u, int v, uint64_t seed)
 {
     uint64_t lo = (uint64_t)(uint32_t)(u < v ? u : v), hi = (uint64_t)(uint32_t)(u < v ? v : u);
@@ -328,7 +355,7 @@ uint64_t or_edge_hash(int u, int v, uint64_t seed)
 }
 
 int64_t or_match(int n, const int64_t *rp, const int32_t *ci, const double *v,
-                 uint64_t seed, int32_t *mate)
+                 uint64_t seed, int scaled, int32_t *mate)
 {
     int64_t *arp; int32_t *aci;
     sym_adjacency(n, rp, ci, &arp, &aci);
@@ -338,7 +365,7 @@ int64_t or_match(int n, const int64_t *rp, const int32_t *ci, const double *v,
         for (int64_t e = arp[u]; e < arp[u + 1]; ++e) {
             int w_ = aci[e];
             if (w_ <= u) continue;
-            double w = or_edge_weight(rp, ci, v, u, w_);
+            double w = or_edge_key_weight(rp, ci, v, u, w_, scaled);
             if (!(w > 0.0)) continue;
             E[ne].w = w; E[ne].hkey = or_edge_hash(u, w_, seed); E[ne].u = u; E[ne].v = w_;
             ++ne;
@@ -878,7 +905,7 @@ void or_free(or_hier_t *H)
 
 /* Aggregate level L by `passes` matching passes; fills L->agg and returns
  * the next level's matrix in *next. */
-static void coarsen_level(or_level_t *L, int passes, uint64_t seed, or_csr_t *next)
+static void coarsen_level(or_level_t *L, int passes, uint64_t seed, int scaled, or_csr_t *next)
 {
     int n = L->A.n;
     or_csr_t cur = L->A;   /* borrowed */
@@ -889,7 +916,7 @@ static void coarsen_level(or_level_t *L, int passes, uint64_t seed, or_csr_t *ne
     for (int p = 0; p < passes; ++p) {
         int m = cur.n;
         int32_t *mate = malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
-        or_match(m, cur.rp, cur.ci, cur.v, seed, mate);
+        or_match(m, cur.rp, cur.ci, cur.v, seed, scaled, mate);
         L->agg_pass[p] = malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
         int nc = or_aggregate(m, mate, L->agg_pass[p]);
         free(mate);
@@ -910,7 +937,8 @@ or_hier_t *or_setup(int n, const int64_t *rp, const int32_t *ci, const double *v
                     const int32_t *opt, double ilut_tau, uint64_t seed, int *status)
 {
     /* opt: [passes, coarse_inner, deep_inner, dense_max, max_levels,
-     *       order_fine, order_coarse, coloring, coarse_solver]
+     *       order_fine, order_coarse, coloring, coarse_solver, match_weight]
+     * match_weight: 0 = plain edge weights, 1 = scaled (see O2).
      * order: 0 = colour-major (hash or first-fit colouring), 1 = natural.
      * coarse_solver: 0 = the recursive Richardson coarse solve; 1 = the
      * paper's two-grid form (Section 2, Algorithm 1): level 1 is the last
@@ -918,11 +946,11 @@ or_hier_t *or_setup(int n, const int64_t *rp, const int32_t *ci, const double *v
     *status = OR_OK;
     int passes = opt[0], coarse_inner = opt[1], deep_inner = opt[2], dense_max = opt[3];
     int max_levels = opt[4], order_fine = opt[5], order_coarse = opt[6], coloring = opt[7];
-    int coarse_ilut = opt[8];
+    int coarse_ilut = opt[8], scaled = opt[9];
     if (coarse_ilut) max_levels = 2;
     if (n <= 0 || passes < 1 || passes > OR_MAX_PASSES || coarse_inner < 1 || deep_inner < 1 ||
         dense_max < 0 || max_levels < 2 || max_levels > OR_MAX_LEVELS || coarse_ilut < 0 || coarse_ilut > 1 ||
-        (coarse_ilut && !(ilut_tau >= 0.0))) { *status = OR_EINVAL; return NULL; }
+        (coarse_ilut && !(ilut_tau >= 0.0)) || scaled < 0 || scaled > 1) { *status = OR_EINVAL; return NULL; }
     if (or_check_csr(n, rp, ci) != OR_OK) { *status = OR_EINVAL; return NULL; }
     or_hier_t *H = calloc(1, sizeof(or_hier_t));
     H->passes = passes; H->coarse_inner = coarse_inner; H->deep_inner = deep_inner;
@@ -936,7 +964,7 @@ or_hier_t *or_setup(int n, const int64_t *rp, const int32_t *ci, const double *v
         int last = (l > 0 && L->A.n <= dense_max) || (l + 1 >= max_levels);
         if (!last) {
             or_csr_t next;
-            coarsen_level(L, passes, seed, &next);
+            coarsen_level(L, passes, seed, scaled, &next);
             if (l > 0 && (double)next.n > 0.9 * (double)L->A.n) {
                 /* matching no longer coarsens: this level is the last one */
                 csr_free(&next);

@@ -16,7 +16,7 @@ from typing import Optional
 import numpy as np
 
 from . import _lib
-from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_COARSE_ILUT, AMG_COARSE_RECURSIVE, AMG_ORTHO_CGS2, AMG_ORTHO_MGS, AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
+from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_MATCH_PLAIN, AMG_MATCH_SCALED, AMG_COARSE_ILUT, AMG_COARSE_RECURSIVE, AMG_ORTHO_CGS2, AMG_ORTHO_MGS, AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
                    AMG_ERR_CUDA, AMG_ERR_INVALID_ARG, AMG_ERR_LIMIT, AMG_ERR_NOT_CONVERGED,
                    AMG_ERR_NOT_SUPPORTED, AMG_ERR_NUMERIC, AMG_ERR_OOM, AMG_FP32, AMG_FP64, AMG_OK,
                    AMG_ORDER_COLOR, AMG_ORDER_NATURAL, AmgCsr, AmgOptions, AmgStats)
@@ -25,7 +25,8 @@ __all__ = [
     "AmgError", "Handle", "amg_default_options", "amg_setup", "amg_destroy", "amg_solve",
     "amg_adjoint", "amg_get_history", "amg_precond_apply", "amg_spmv", "amg_get_level_info",
     "amg_num_levels", "amg_get_aggregates", "amg_get_matrix", "amg_get_pass_matrix",
-    "amg_get_colors", "amg_get_ilu", "amg_fv_assemble", "amg_fv_grad_logk", "amg_version",
+    "amg_get_colors", "amg_get_ilu", "amg_fv_assemble", "amg_fv_grad_logk", "amg_fv_assemble_logk",
+    "amg_fv_grad_logk_iso", "amg_version",
     "amg_status_string", "lib", "amg_set_kernel_timing", "amg_get_kernel_timing",
     "amg_launch_counter", "amg_csr_value_grad", "amg_spmv_noalloc", "amg_setup_batched",
     "amg_solve_batched", "amg_batch_size", "amg_batch_member", "amg_get_spmv_config",
@@ -390,5 +391,25 @@ def amg_fv_grad_logk(dim, nx, ny, nz, kx, ky, kz, lam, x, gx, gy, gz=None, strea
                                   _ptr(gx), _ptr(gy), _ptr(gz), stream), "amg_fv_grad_logk")
 
 
-from .device import CsrDevice, assemble_fv, solve  # noqa: E402,F401
+def amg_fv_assemble_logk(dim, nx, ny, nz, logk, kappa, fx, fy, fz, f, row_ptr, col, val, b, stream=None) -> int:
+    """amg_fv_assemble_logk on device tensors (kappa = exp(logk) written to
+    `kappa`); returns nnz."""
+    nnz = C.c_int64(0)
+    if stream is None:
+        stream = _stream_of(logk)
+    _check(lib().amg_fv_assemble_logk(dim, nx, ny, nz, _ptr(logk, "float64"), _ptr(kappa, "float64"), _ptr(fx),
+                                      _ptr(fy), _ptr(fz), _ptr(f), _ptr(row_ptr, "int64"), _ptr(col, "int32"),
+                                      _ptr(val, "float64"), _ptr(b, "float64"), C.byref(nnz), stream),
+           "amg_fv_assemble_logk")
+    return nnz.value
+
+
+def amg_fv_grad_logk_iso(dim, nx, ny, nz, kappa, lam, x, g, stream=None):
+    if stream is None:
+        stream = _stream_of(kappa)
+    _check(lib().amg_fv_grad_logk_iso(dim, nx, ny, nz, _ptr(kappa, "float64"), _ptr(lam, "float64"),
+                                      _ptr(x, "float64"), _ptr(g, "float64"), stream), "amg_fv_grad_logk_iso")
+
+
+from .device import CsrDevice, assemble_fv, assemble_fv_logk, solve  # noqa: E402,F401
 from .autograd import AmgSolve, FvLogKappaSolve  # noqa: E402,F401

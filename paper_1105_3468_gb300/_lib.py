@@ -28,6 +28,7 @@ AMG_ORDER_COLOR, AMG_ORDER_NATURAL = 0, 1
 AMG_COLOR_HASH_JP, AMG_COLOR_FIRST_FIT = 0, 1
 AMG_ORTHO_MGS, AMG_ORTHO_CGS2 = 0, 1
 AMG_COARSE_RECURSIVE, AMG_COARSE_ILUT = 0, 1
+AMG_MATCH_PLAIN, AMG_MATCH_SCALED = 0, 1
 
 
 class AmgCsr(C.Structure):
@@ -42,7 +43,7 @@ class AmgOptions(C.Structure):
                 ("maxit", C.c_int32), ("vcycle_prec", C.c_int32), ("build_adjoint", C.c_int32),
                 ("use_graphs", C.c_int32), ("persistent", C.c_int32), ("deep_block_max", C.c_int32),
                 ("orthog", C.c_int32), ("spmv_block", C.c_int32), ("spmv_unroll", C.c_int32),
-                ("dot2", C.c_int32), ("reserved0", C.c_int32),
+                ("dot2", C.c_int32), ("match_weight", C.c_int32),
                 ("seed", C.c_uint64), ("coarse_solver", C.c_int32), ("reserved1", C.c_int32),
                 ("ilut_tau", C.c_double)]
 
@@ -96,6 +97,8 @@ SIGNATURES = {
     "amg_fv_assemble": (C.c_int, [C.c_int32] * 4 + [_P] * 7 + [_P, _P, _P, _P, C.POINTER(C.c_int64), _P]),
     "amg_csr_value_grad": (C.c_int, [C.POINTER(AmgCsr), _P, _P, _P, _P]),
     "amg_fv_grad_logk": (C.c_int, [C.c_int32] * 4 + [_P] * 8 + [_P]),
+    "amg_fv_assemble_logk": (C.c_int, [C.c_int32] * 4 + [_P] * 6 + [_P, _P, _P, _P, C.POINTER(C.c_int64), _P]),
+    "amg_fv_grad_logk_iso": (C.c_int, [C.c_int32] * 4 + [_P] * 4 + [_P]),
 }
 
 _lock = threading.Lock()

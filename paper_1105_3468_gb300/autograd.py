@@ -6,14 +6,34 @@ transposed ILU(0) smoother), then
   dL/db = lambda,  dL/dA_ij = -lambda_i x_j on the sparsity pattern
 (amg_csr_value_grad), or, for the finite-volume problem, the chain through
 the harmonic-mean transmissibilities to per-cell log-conductivities
-(amg_fv_grad_logk).  All arithmetic runs in the library's kernels.
+(amg_fv_grad_logk_iso).  All arithmetic runs in the library's kernels: the
+binding only passes device buffers.
+
+Handle lifetime: the hierarchy built in forward lives as long as the autograd
+graph that holds it (it is released with the graph, or at once when no input
+needs a gradient), so a second backward with retain_graph=True reuses it.
 """
 from __future__ import annotations
 
 import torch
 
-from . import (amg_adjoint, amg_csr_value_grad, amg_fv_grad_logk, amg_setup, amg_solve)
-from .device import CsrDevice, assemble_fv
+from . import (amg_adjoint, amg_csr_value_grad, amg_fv_grad_logk_iso, amg_setup, amg_solve)
+from .device import CsrDevice, assemble_fv_logk
+
+
+def _keep_handle(ctx, h):
+    if any(ctx.needs_input_grad):
+        ctx.h = h
+    else:
+        h.close()
+        ctx.h = None
+
+
+def _handle(ctx):
+    h = getattr(ctx, "h", None)
+    if h is None or not h.ptr.value:
+        raise RuntimeError("the hierarchy of this solve was released: no input required a gradient")
+    return h
 
 
 class AmgSolve(torch.autograd.Function):
@@ -25,7 +45,8 @@ class AmgSolve(torch.autograd.Function):
         h = amg_setup(A, opts, build_adjoint=1)
         x = torch.zeros_like(b)
         st = amg_solve(h, b.detach().contiguous(), x, tol)
-        ctx.h, ctx.A, ctx.tol, ctx.stats = h, A, tol, st
+        ctx.A, ctx.tol, ctx.stats = A, tol, st
+        _keep_handle(ctx, h)
         ctx.save_for_backward(x)
         return x
 
@@ -33,29 +54,26 @@ class AmgSolve(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         lam = torch.zeros_like(x)
-        amg_adjoint(ctx.h, gx.contiguous(), lam, ctx.tol)
+        amg_adjoint(_handle(ctx), gx.contiguous(), lam, ctx.tol)
         gval = torch.empty_like(ctx.A.val)
         amg_csr_value_grad(ctx.A, lam, x, gval)
-        ctx.h.close()
         return gval, lam, None, None, None, None
 
 
 class FvLogKappaSolve(torch.autograd.Function):
-    """x(log kappa) for an isotropic block-kappa grid problem: assemble eq. (2)
-    on the GPU from exp(log kappa), solve, and differentiate through the
-    adjoint solve and the transmissibilities."""
+    """x(log kappa) for an isotropic grid problem: kappa = exp(log kappa) and
+    the assembly of eq. (2) on the GPU (amg_fv_assemble_logk), the solve, and
+    the derivative through the adjoint solve and the transmissibilities
+    (amg_fv_grad_logk_iso)."""
 
     @staticmethod
     def forward(ctx, logk, prob, tol=1e-10, opts=None):
-        import dataclasses
-        k = torch.exp(logk.detach()).contiguous()
-        kn = k.cpu().numpy()
-        p = dataclasses.replace(prob, kx=kn, ky=kn, kz=kn)
-        A, b = assemble_fv(p, device=logk.device)
+        A, b, kappa = assemble_fv_logk(prob, logk)
         h = amg_setup(A, opts, build_adjoint=1)
         x = torch.zeros_like(b)
         st = amg_solve(h, b, x, tol)
-        ctx.h, ctx.prob, ctx.k, ctx.tol, ctx.stats = h, prob, k, tol, st
+        ctx.prob, ctx.kappa, ctx.tol, ctx.stats = prob, kappa, tol, st
+        _keep_handle(ctx, h)
         ctx.save_for_backward(x)
         return x
 
@@ -63,12 +81,8 @@ class FvLogKappaSolve(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         lam = torch.zeros_like(x)
-        amg_adjoint(ctx.h, gx.contiguous(), lam, ctx.tol)
-        p, k = ctx.prob, ctx.k
-        gs = [torch.zeros_like(x) for _ in range(3)]
-        kz = k if p.dim == 3 else None
-        amg_fv_grad_logk(p.dim, p.nx, p.ny, p.nz, k, k, kz, lam, x, gs[0], gs[1],
-                         gs[2] if p.dim == 3 else None)
-        g = gs[0] + gs[1] + (gs[2] if p.dim == 3 else 0)
-        ctx.h.close()
+        amg_adjoint(_handle(ctx), gx.contiguous(), lam, ctx.tol)
+        p = ctx.prob
+        g = torch.empty_like(x)
+        amg_fv_grad_logk_iso(p.dim, p.nx, p.ny, p.nz, ctx.kappa, lam, x, g)
         return g, None, None, None

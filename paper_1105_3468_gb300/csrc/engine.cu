@@ -221,7 +221,7 @@ static void coarsen(Level &L, const amg_options_t &o, DBuf<int> &adj_rp, DBuf<in
             nc = F.n_out;
         } else {
             DBuf<int> mate(cur->n);
-            match_pass(*cur, arp.get(), aci.get(), annz, o.seed, mate.get(), s);
+            match_pass(*cur, arp.get(), aci.get(), annz, o.seed, o.match_weight, mate.get(), s);
             P.agg.alloc(cur->n);
             nc = aggregates_from_mate(cur->n, mate.get(), P.agg.get(), s);
         }
@@ -1117,7 +1117,7 @@ int amg_default_options(amg_options_t *o) {
     o->spmv_block = 0;
     o->spmv_unroll = 0;
     o->dot2 = -1;
-    o->reserved0 = 0;
+    o->match_weight = AMG_MATCH_SCALED;
     o->seed = 0;
     o->coarse_solver = AMG_COARSE_RECURSIVE;
     o->reserved1 = 0;
@@ -1134,7 +1134,7 @@ static void check_options(const amg_options_t &o) {
         (o.spmv_block != 0 && o.spmv_block != 64 && o.spmv_block != 128 && o.spmv_block != 256 &&
          o.spmv_block != 512) ||
         (o.spmv_unroll != 0 && o.spmv_unroll != 2 && o.spmv_unroll != 4 && o.spmv_unroll != 8) || o.dot2 < -1 ||
-        o.dot2 > 1 || o.coarse_solver < 0 || o.coarse_solver > 1 || !(o.ilut_tau >= 0.0) ||
+        o.dot2 > 1 || o.match_weight < 0 || o.match_weight > 1 || o.coarse_solver < 0 || o.coarse_solver > 1 || !(o.ilut_tau >= 0.0) ||
         !std::isfinite(o.ilut_tau))
         fail(AMG_ERR_INVALID_ARG, "option out of range (restart <= 31, dense_max <= 4096, 2 <= max_levels <= 24)");
 }
@@ -1556,6 +1556,22 @@ int amg_fv_assemble(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const doubl
     ABI_CATCH
 }
 
+int amg_fv_assemble_logk(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *logk, double *kappa,
+                         const double *fx, const double *fy, const double *fz, const double *f, int64_t *row_ptr,
+                         int32_t *col, double *val, double *b, int64_t *nnz_out, void *stream) {
+    ABI_TRY
+    if ((dim != 2 && dim != 3) || nx <= 0 || ny <= 0 || nz <= 0 || (dim == 2 && nz != 1))
+        fail(AMG_ERR_INVALID_ARG, "amg_fv_assemble_logk: bad grid");
+    if ((int64_t)nx * ny * nz * (2 * dim + 1) >= (int64_t)0x7fffffff) fail(AMG_ERR_INVALID_ARG, "grid too large");
+    if (!logk || !kappa || !fx || !fy || !f || !row_ptr || !col || !val || !b || !nnz_out || (dim == 3 && !fz))
+        fail(AMG_ERR_INVALID_ARG, "amg_fv_assemble_logk: null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    exp_f64((long)nx * ny * nz, logk, kappa, s);
+    *nnz_out = fv_assemble(dim, nx, ny, nz, kappa, kappa, kappa, fx, fy, fz, f, row_ptr, col, val, b, s);
+    return AMG_OK;
+    ABI_CATCH
+}
+
 __global__ void k_csr_outer_grad(int n, const int64_t *rp, const int32_t *ci, const double *lam, const double *x,
                                  double *g) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1584,6 +1600,18 @@ int amg_fv_grad_logk(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const doub
     if (!kx || !ky || !lambda || !x || !gx || !gy || (dim == 3 && (!kz || !gz)))
         fail(AMG_ERR_INVALID_ARG, "amg_fv_grad_logk: null pointer");
     fv_grad_logk(dim, nx, ny, nz, kx, ky, kz, lambda, x, gx, gy, gz, (cudaStream_t)stream);
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_fv_grad_logk_iso(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *kappa,
+                         const double *lambda, const double *x, double *g, void *stream) {
+    ABI_TRY
+    if ((dim != 2 && dim != 3) || nx <= 0 || ny <= 0 || nz <= 0 || (dim == 2 && nz != 1))
+        fail(AMG_ERR_INVALID_ARG, "amg_fv_grad_logk_iso: bad grid");
+    if (!kappa || !lambda || !x || !g) fail(AMG_ERR_INVALID_ARG, "amg_fv_grad_logk_iso: null pointer");
+    fv_grad_logk(dim, nx, ny, nz, kappa, kappa, kappa, lambda, x, g, nullptr, nullptr, (cudaStream_t)stream);
     CU(cudaStreamSynchronize((cudaStream_t)stream));
     return AMG_OK;
     ABI_CATCH

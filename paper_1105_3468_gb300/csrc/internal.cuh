@@ -131,9 +131,11 @@ int csr_validate(int n, const int *rp, const int *ci, cudaStream_t s);
 // Symmetrised off-diagonal adjacency of the pattern (A + A^T, no diagonal).
 void sym_adjacency(const DCsr &A, DBuf<int> &arp, DBuf<int> &aci, int &annz, cudaStream_t s);
 
-// One heavy-edge matching pass; mate[u] = partner or -1.  Returns rounds or
-// throws AMG_ERR_LIMIT.
-int match_pass(const DCsr &A, const int *arp, const int *aci, int annz, uint64_t seed,
+// One heavy-edge matching pass; mate[u] = partner or -1.  scaled: edge
+// weights divided by the geometric mean of their endpoints' diagonal
+// magnitudes.
+// Returns rounds or throws AMG_ERR_LIMIT.
+int match_pass(const DCsr &A, const int *arp, const int *aci, int annz, uint64_t seed, int scaled,
                int *mate, cudaStream_t s);
 
 // Aggregates from a matching: agg[u], returns N_c.
@@ -178,9 +180,12 @@ void cast_f64_bf16(const double *in, __nv_bfloat16 *out, size_t n, cudaStream_t 
 int64_t fv_assemble(int dim, int nx, int ny, int nz, const double *kx, const double *ky,
                     const double *kz, const double *fx, const double *fy, const double *fz,
                     const double *f, int64_t *rp, int *ci, double *v, double *b, cudaStream_t s);
+// gy == nullptr: isotropic conductivity kx per cell; gx receives the
+// derivative with respect to log kx (the sum of the three axis terms).
 void fv_grad_logk(int dim, int nx, int ny, int nz, const double *kx, const double *ky,
                   const double *kz, const double *lam, const double *x, double *gx, double *gy,
                   double *gz, cudaStream_t s);
+void exp_f64(long n, const double *in, double *out, cudaStream_t s);
 
 // ------------------------------------------------------------------ kernels: solve
 // Grid sizing helper: blocks for n items at `tpb` threads, capped to a

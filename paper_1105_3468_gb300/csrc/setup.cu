@@ -116,15 +116,23 @@ void sym_adjacency(const DCsr &A, DBuf<int> &arp, DBuf<int> &aci, int &annz, cud
 }
 
 // ------------------------------------------------------------------ matching
-// Edge {u,v}, u < v: w = (|a_uv| + |a_vu|) * 0.5, missing entry = 0; key
+// Edge {u,v}, u < v: w = (|a_uv| + |a_vu|) * 0.5, missing entry = 0; with the
+// scaled weight (scaled = 1) w is divided by sqrt(|a_uu| |a_vv|) (the product
+// rounded, then the correctly rounded square root), the strength of
+// connection of smoothed aggregation (Vanek, Mandel, Brezina 1996); key
 // (w, mix64(((u<<32)|v) ^ seed), u, v), larger first.  Each round, every
 // free vertex proposes to its largest-key free neighbour; mutual proposals
 // are matched.  Mutual maxima of a strict total order are exactly the
 // edges a greedy pass in decreasing key order takes, so the fixed point is
 // the greedy matching.
 __global__ void k_edge_weights(int n, const int *rp, const int *ci, const double *v, const int *arp,
-                               const int *aci, double *aw) {
+                               const int *aci, int scaled, double *aw) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        double du = 0.0;
+        if (scaled) {
+            int eu = find_col(ci, rp[u], rp[u + 1], u);
+            du = eu >= 0 ? fabs(v[eu]) : 0.0;
+        }
         for (int e = arp[u]; e < arp[u + 1]; ++e) {
             int w = aci[e];
             int lo = u < w ? u : w, hi = u < w ? w : u;
@@ -132,7 +140,13 @@ __global__ void k_edge_weights(int n, const int *rp, const int *ci, const double
             int e2 = find_col(ci, rp[hi], rp[hi + 1], lo);
             double a1 = e1 >= 0 ? fabs(v[e1]) : 0.0;
             double a2 = e2 >= 0 ? fabs(v[e2]) : 0.0;
-            aw[e] = __dmul_rn(__dadd_rn(a1, a2), 0.5);
+            double wt = __dmul_rn(__dadd_rn(a1, a2), 0.5);
+            if (scaled && wt > 0.0) {
+                int ew = find_col(ci, rp[w], rp[w + 1], w);
+                double dw = ew >= 0 ? fabs(v[ew]) : 0.0;
+                wt = __ddiv_rn(wt, __dsqrt_rn(__dmul_rn(du, dw)));
+            }
+            aw[e] = wt;
         }
     }
 }
@@ -185,12 +199,13 @@ __global__ void k_unmark_dead(int n, int *mate) {
         if (mate[u] < 0) mate[u] = -1;
 }
 
-int match_pass(const DCsr &A, const int *arp, const int *aci, int annz, uint64_t seed, int *mate,
+int match_pass(const DCsr &A, const int *arp, const int *aci, int annz, uint64_t seed, int scaled, int *mate,
                cudaStream_t s) {
     const int n = A.n;
     DBuf<double> aw(annz > 0 ? annz : 1);
     DBuf<int> prop(n), active(1);
-    k_edge_weights<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), arp, aci, aw.get());
+    k_edge_weights<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), arp, aci, scaled,
+                                                   aw.get());
     CU_LAUNCH("k_edge_weights"); count_launch();
     fill_int(mate, -1, n, s);
     int *hactive = nullptr;
@@ -1154,6 +1169,10 @@ int64_t fv_assemble(int dim, int nx, int ny, int nz, const double *kx, const dou
     return nnz;
 }
 
+// ISO: kx = ky = kz = kappa (one conductivity per cell), and the derivative
+// with respect to log kappa is the sum of the per-axis ones, added in axis
+// order (x + y) + z into gx; gy, gz are not written.
+template <bool ISO>
 __global__ void k_fv_grad(FvGrid g, const double *kx, const double *ky, const double *kz, const double *lam,
                           const double *x, double *gx, double *gy, double *gz) {
     const long N = (long)g.nx * g.ny * g.nz;
@@ -1162,6 +1181,7 @@ __global__ void k_fv_grad(FvGrid g, const double *kx, const double *ky, const do
         int c[3] = {(int)(P % g.nx), (int)((P / g.nx) % g.ny), (int)(P / sxy)};
         int dims[3] = {g.nx, g.ny, g.nz};
         long stride[3] = {1, g.nx, sxy};
+        double iso = 0.0;
         for (int axis = 0; axis < g.dim; ++axis) {
             const double *kk = axis == 0 ? kx : (axis == 1 ? ky : kz);
             double acc = 0.0;
@@ -1181,10 +1201,25 @@ __global__ void k_fv_grad(FvGrid g, const double *kx, const double *ky, const do
                 double dLdT = __dmul_rn(-__dsub_rn(lam[P], lam[Q]), __dsub_rn(x[P], x[Q]));
                 acc = __dadd_rn(acc, __dmul_rn(dLdT, __ddiv_rn(__dmul_rn(T, kN), __dadd_rn(kP, kN))));
             }
-            double *gg = axis == 0 ? gx : (axis == 1 ? gy : gz);
-            gg[P] = acc;
+            if (ISO) {
+                iso = axis == 0 ? acc : __dadd_rn(iso, acc);
+            } else {
+                double *gg = axis == 0 ? gx : (axis == 1 ? gy : gz);
+                gg[P] = acc;
+            }
         }
+        if (ISO) gx[P] = iso;
     }
+}
+
+__global__ void k_exp(long n, const double *in, double *out) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        out[i] = exp(in[i]);
+}
+
+void exp_f64(long n, const double *in, double *out, cudaStream_t s) {
+    k_exp<<<grid_for(n, 256), 256, 0, s>>>(n, in, out);
+    CU_LAUNCH("k_exp"); count_launch();
 }
 
 void fv_grad_logk(int dim, int nx, int ny, int nz, const double *kx, const double *ky, const double *kz,
@@ -1195,7 +1230,10 @@ void fv_grad_logk(int dim, int nx, int ny, int nz, const double *kx, const doubl
     g.hd2 = dim == 2 ? 1.0 : h;
     g.hd = dim == 2 ? h * h : h * h * h;
     const long N = (long)nx * ny * nz;
-    k_fv_grad<<<grid_for(N, 256), 256, 0, s>>>(g, kx, ky, kz, lam, x, gx, gy, gz);
+    if (gy)
+        k_fv_grad<false><<<grid_for(N, 256), 256, 0, s>>>(g, kx, ky, kz, lam, x, gx, gy, gz);
+    else
+        k_fv_grad<true><<<grid_for(N, 256), 256, 0, s>>>(g, kx, kx, kx, lam, x, gx, nullptr, nullptr);
     CU_LAUNCH("k_fv_grad"); count_launch();
 }
 

@@ -54,6 +54,32 @@ def assemble_fv(prob, device="cuda"):
     return CsrDevice(N, rp, ci[:nnz].clone(), v[:nnz].clone()), b
 
 
+def assemble_fv_logk(prob, logk):
+    """Assemble eq. (2) on the GPU for an isotropic conductivity given as the
+    device tensor `logk` (amg_fv_assemble_logk: exp and assembly in the
+    library); the grid, fluxes and source come from `prob`.  Returns
+    (A, b, kappa) with kappa = exp(logk) on the device."""
+    import torch
+    from . import amg_fv_assemble_logk
+    device = logk.device
+
+    def dev(a):
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+
+    N = prob.nx * prob.ny * prob.nz
+    cap = (2 * prob.dim + 1) * N
+    rp = torch.empty(N + 1, dtype=torch.int64, device=device)
+    ci = torch.empty(cap, dtype=torch.int32, device=device)
+    v = torch.empty(cap, dtype=torch.float64, device=device)
+    b = torch.empty(N, dtype=torch.float64, device=device)
+    kappa = torch.empty(N, dtype=torch.float64, device=device)
+    fz = dev(prob.fz) if prob.dim == 3 else None
+    lk = logk.detach().to(torch.float64).contiguous()
+    nnz = amg_fv_assemble_logk(prob.dim, prob.nx, prob.ny, prob.nz, lk, kappa, dev(prob.fx), dev(prob.fy), fz,
+                               dev(prob.f), rp, ci, v, b)
+    return CsrDevice(N, rp, ci[:nnz].clone(), v[:nnz].clone()), b, kappa
+
+
 def solve(A, b, x0=None, tol: float = 1e-8, opts=None, **overrides):
     """Set up and solve A x = b once; returns (x, stats, history)."""
     import torch

@@ -46,7 +46,7 @@ def env():
 CASES = {
     # problem, options of the benchmark for it (GPU name -> oracle name)
     "c3": (lambda: W.c3_aniso_3d_128(), {}),
-    "c2": (lambda: W.c2_rotating_2d_1024(), {"order_fine": 0}),
+    "c2": (lambda: W.c2_rotating_2d_1024(), {"order_fine": 0, "match_weight": 0}),
 }
 
 

@@ -90,6 +90,17 @@ def test_setup_bit_exact(env, name):
     check_hierarchy(amg, h, H)
 
 
+@pytest.mark.parametrize("name", ["rot2d-100", "dc1-2d-80"])
+def test_setup_bit_exact_plain_weights(env, name):
+    """The unscaled matching weights (AMG_MATCH_PLAIN) give the oracle's
+    hierarchy bit for bit as well."""
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, name)
+    h = amg.amg_setup(A, match_weight=amg.AMG_MATCH_PLAIN)
+    H = O.Hierarchy(Ao, match_weight=O.MATCH_PLAIN)
+    check_hierarchy(amg, h, H)
+
+
 def test_setup_bit_exact_rgg_and_first_fit(env):
     amg, O, torch = env
     A = W.rgg_matrix(4099, 11, seed=8)

@@ -5,10 +5,17 @@ Matching (aggregation by graph matching, Section 2):
   the SplitMix64 generator from state 0 are its published test vectors;
 * validity (each vertex in at most one pair; every pair an edge, w > 0) and
   maximality (no edge joins two unmatched vertices);
-* brute force on small graphs: the greedy matching equals the matching whose
-  key multiset, sorted in decreasing order, is lexicographically largest;
+* brute force on small graphs, for the plain and the scaled edge weight: the
+  greedy matching equals the matching whose key multiset, sorted in
+  decreasing order, is lexicographically largest (keys recomputed here from
+  the dense matrix);
 * the weight of a structurally one-sided entry is |a_uv|/2; A and A^T give
-  the same matching.
+  the same matching;
+* scaled weight, hand-computed: a vertex whose coupling is all of its
+  diagonal pairs with its neighbour even against a heavier plain weight;
+* scaled weight on the paper's DC1 2D case at 640^2: every level shrinks by
+  at least 2x down to fewer than 200 rows, where the plain weight stalls
+  (a level shrinking by less than 10%).
 Aggregates (eq. (4) and the part map of Section 2): a partition; P*1 = 1;
 rank P = N_c (Theorem 1); size <= 2^passes; ids ordered by smallest member.
 Galerkin (eq. (3) and its entrywise form, Section 2): brute-force dense
@@ -53,8 +60,9 @@ def _random_sparse(rng, n, density, sym_pattern=True, dyadic=False):
     return D
 
 
-def _edges(O, A):
-    """Unordered structural edges with their keys (weight, hash, u, v)."""
+def _edges(O, A, scaled=1):
+    """Unordered structural edges with their keys (weight, hash, u, v); the
+    weights are computed here from the dense matrix."""
     D = A.dense()
     n = A.n
     pat = (np.abs(D) > 0) | (np.abs(D.T) > 0)
@@ -62,26 +70,29 @@ def _edges(O, A):
     for u in range(n):
         for v in range(u + 1, n):
             if pat[u, v]:
-                w = O.edge_weight(A, u, v)
+                w = (abs(D[u, v]) + abs(D[v, u])) * 0.5
+                if scaled and w > 0:
+                    w = w / np.sqrt(abs(D[u, u]) * abs(D[v, v]))
                 if w > 0:
                     out.append(((w, O.edge_hash(u, v, 0), u, v), u, v))
     return out
 
 
-def _check_matching(O, A, mate):
+def _check_matching(O, A, mate, scaled=1):
     n = A.n
     for u in range(n):
         if mate[u] >= 0:
             assert mate[mate[u]] == u and mate[u] != u
-    for key, u, v in _edges(O, A):
+    for key, u, v in _edges(O, A, scaled):
         assert not (mate[u] < 0 and mate[v] < 0), "not maximal"
     pairs = {(min(u, int(mate[u])), max(u, int(mate[u]))) for u in range(n) if mate[u] >= 0}
-    edge_set = {(u, v) for _, u, v in _edges(O, A)}
+    edge_set = {(u, v) for _, u, v in _edges(O, A, scaled)}
     assert pairs <= edge_set
 
 
+@pytest.mark.parametrize("scaled", [0, 1])
 @pytest.mark.parametrize("seed", range(12))
-def test_matching_brute_force(oracle_lib, seed):
+def test_matching_brute_force(oracle_lib, seed, scaled):
     O = oracle_lib
     rng = np.random.default_rng(seed)
     n = int(rng.integers(3, 9))
@@ -89,10 +100,12 @@ def test_matching_brute_force(oracle_lib, seed):
     if seed % 3 == 0:   # ties in weight: the hash decides
         D[np.abs(D) > 0] = np.sign(D[np.abs(D) > 0])
         np.fill_diagonal(D, 10.0)
+    elif scaled:        # unequal diagonals, so scaling reorders the keys
+        np.fill_diagonal(D, np.diag(D) * rng.uniform(0.5, 4.0, n))
     A = O.as_csr(D)
-    mate = O.match(A)
-    _check_matching(O, A, mate)
-    E = _edges(O, A)
+    mate = O.match(A, weight=scaled)
+    _check_matching(O, A, mate, scaled)
+    E = _edges(O, A, scaled)
     best = None
     for r in range(0, n // 2 + 1):
         for combo in itertools.combinations(range(len(E)), r):
@@ -124,9 +137,44 @@ def test_matching_one_sided_weight_and_transpose(oracle_lib):
     A = O.as_csr(D)
     assert O.edge_weight(A, 0, 1) == 1.5
     assert O.edge_weight(A, 1, 0) == 1.5
-    mate = O.match(A)
-    assert mate.tolist() == [1, 0, 3, 2]
-    assert np.array_equal(O.match(O.as_csr(D.T.copy())), mate)
+    assert O.edge_key_weight(A, 0, 1, 0) == 1.5 and O.edge_key_weight(A, 0, 1, 1) == 1.5 / 4.0   # sqrt(4*4)
+    for scaled in (0, 1):
+        mate = O.match(A, weight=scaled)
+        assert mate.tolist() == [1, 0, 3, 2]
+        assert np.array_equal(O.match(O.as_csr(D.T.copy()), weight=scaled), mate)
+
+
+def test_scaled_weight_pairs_a_dominated_vertex(oracle_lib):
+    """Path 0 - 1 - 2: vertex 0's only coupling (1) is its whole diagonal,
+    while 1 - 2 carries the heavier coupling 3 to a vertex with a large
+    diagonal (100).  Plain weights (1 vs 3) pair {1, 2} and leave 0 single;
+    scaled weights (1/sqrt(1*4) = 0.5 vs 3/sqrt(4*100) = 0.15) pair {0, 1}."""
+    O = oracle_lib
+    D = np.array([[1.0, -1.0, 0.0], [-1.0, 4.0, -3.0], [0.0, -3.0, 100.0]])
+    A = O.as_csr(D)
+    assert O.edge_key_weight(A, 0, 1, 1) == 0.5
+    assert O.edge_key_weight(A, 1, 2, 1) == 3.0 / 20.0
+    assert O.match(A, weight=0).tolist() == [-1, 2, 1]
+    assert O.match(A, weight=1).tolist() == [1, 0, -1]
+
+
+def test_scaled_weight_does_not_stall_on_dc1():
+    """The paper's DC1 2D case (Section 4) at 640^2, coarsened without a
+    dense level: with scaled weights each level of at least 200 rows is
+    followed by one of at most half its size, down to fewer than 200 rows;
+    with plain weights some level keeps more than 90% (the stall that ends
+    the hierarchy)."""
+    import oracle as O
+    A, _ = O.fv_assemble(W.dc_problem(640, 2))
+    for scaled in (1, 0):
+        H = O.Hierarchy(A, dense_max=0, max_levels=24, match_weight=scaled)
+        sizes = [L["n"] for L in H.levels]
+        ratios = [b / a for a, b in zip(sizes, sizes[1:])]
+        if scaled:
+            big = [r for a, r in zip(sizes, ratios) if a >= 200]
+            assert sizes[-1] < 200 and max(big) <= 0.5, sizes
+        else:
+            assert sizes[-1] > 1000, sizes          # the last level is the stalled one
 
 
 def test_matching_on_grid_is_valid_and_maximal(oracle_lib):
