@@ -102,11 +102,22 @@ def run_batch(args, amg, torch):
         if world > 1:
             dist.barrier()
 
+    extra_opts = {}
+    for kv in args.opt:
+        k, v = kv.split("=", 1)
+        extra_opts[k] = float(v) if k == "ilut_tau" else int(v)
+    split = []
+
     def step(prec):
         extra = {"dot2": args.fp64_dot2} if prec == amg.AMG_FP64 and vp != amg.AMG_FP64 else {}
-        h = amg.amg_setup_batched(mats, vcycle_prec=prec, maxit=maxit, **extra)
+        t0 = time.perf_counter()
+        h = amg.amg_setup_batched(mats, vcycle_prec=prec, maxit=maxit, **extra, **extra_opts)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         x = torch.zeros_like(b)
         st = amg.amg_solve_batched(h, b, x, tol)
+        torch.cuda.synchronize()
+        split.append((prec, 1e3 * (t1 - t0), 1e3 * (time.perf_counter() - t1)))
         h.close()
         return st
 
@@ -152,7 +163,9 @@ def run_batch(args, amg, torch):
                       "parallelism": f"members split over {world} ranks (LPT by nnz)" if world > 1 else "single GPU"},
            "rows_per_s": round(rows / (ms * 1e-3)),
            "iters_min_max": [min(i for i, _ in per_member), max(i for i, _ in per_member)],
-           "all_converged": all(s == 0 for _, s in per_member), "gpu_launches": int(launches)}
+           "all_converged": all(s == 0 for _, s in per_member), "gpu_launches": int(launches),
+           "setup_solve_ms_last_step": [[round(a, 1), round(c, 1)] for p, a, c in split if p == vp][-1],
+           "options": extra_opts}
     if amg.AMG_FP64 in res and vp != amg.AMG_FP64:
         out["fp64_ms_per_step"] = round(res[amg.AMG_FP64][0], 2)
     print(json.dumps(out), flush=True)
@@ -255,48 +268,120 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(prob, tol, iters_fp64, sopts, sample_iters=1):
-    """Oracle (single-threaded C, as it stands) on a bounded sample: full-size
-    setup plus `sample_iters` FGMRES iterations, scaled to the iteration count
-    the method needs on this system."""
-    import oracle as O
-    A, b = O.fv_assemble(prob)
-    t0 = time.perf_counter()
-    H = O.Hierarchy(A, **sopts)
-    t1 = time.perf_counter()
-    H.fgmres(b, tol=tol, maxit=sample_iters)
-    t2 = time.perf_counter()
-    per_it = (t2 - t1) / sample_iters
-    value_ms = 1e3 * ((t1 - t0) + per_it * iters_fp64)
+def oracle_iterations(name):
+    """(iterations, detail) of the oracle's own full FP64 solve of workload
+    `name`, from oracle/workload_iters.json (written by
+    oracle/workload_iters.py, which runs only the oracle), or (None, None)."""
+    path = os.path.join(ROOT, "oracle", "workload_iters.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None, None
+    return d.get(name), d.get(name + "_detail")
+
+
+class OracleSample:
+    """The oracle (single-threaded C, as it stands) on a bounded sample of the
+    workload: its full-size setup, timed once, and full FGMRES(m) restart
+    cycles from x0 = 0, each timed on its own (m iterations, the Arnoldi
+    steps j = 1..m and the cycle's update and true residual).  The time of
+    the whole solve is projected as setup + iterations x (cycle time / m),
+    with the iteration count of the oracle's own full solve."""
+
+    def __init__(self, prob, sopts):
+        import oracle as O
+        self.O = O
+        self.A, self.b = O.fv_assemble(prob)
+        t0 = time.perf_counter()
+        self.H = O.Hierarchy(self.A, **sopts)
+        self.setup_s = time.perf_counter() - t0
+
+    def cycle_s(self, m=30):
+        t0 = time.perf_counter()
+        self.H.fgmres(self.b, tol=0.0, restart=m, maxit=m)
+        return (time.perf_counter() - t0) / m
+
+    def describe(self, per_it, cycles, iters, detail, m=30):
+        s = (f"full-size oracle setup ({self.setup_s:.1f} s) + {cycles} full FGMRES({m}) cycle(s) "
+             f"({per_it:.2f} s/iteration averaged over the cycle), projected to the {iters} iterations of the "
+             f"oracle's own full solve; 1 thread on a host with {os.cpu_count()} cores")
+        if detail:
+            s += (f"; cross-check: the oracle's full solve measured by oracle/workload_iters.py on its host took "
+                  f"{detail.get('setup_s', 0) + detail.get('solve_s', 0):.0f} s (setup {detail.get('setup_s')} s)")
+        return s
+
+
+def cpu_baseline(prob, sopts, name):
+    """Oracle timed on a bounded sample (setup + one full restart cycle),
+    projected to the oracle's own iteration count for this workload."""
+    iters, detail = oracle_iterations(name)
+    if iters is None:
+        return None
+    S = OracleSample(prob, sopts)
+    per_it = S.cycle_s()
+    value_ms = 1e3 * (S.setup_s + per_it * iters)
     return {"value": round(value_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": (f"full-size oracle setup ({t1 - t0:.1f} s) + {sample_iters} FGMRES iteration(s) "
-                       f"({per_it:.1f} s/iteration), scaled to the {iters_fp64} iterations the FP64 method "
-                       f"takes on this system; 1 of {os.cpu_count()} host cores")}
+            "sample": S.describe(per_it, 1, iters, detail), "oracle_iters": iters,
+            "setup_s": round(S.setup_s, 2), "s_per_iteration": round(per_it, 4)}
+
+
+def companion_errors(amg, torch, opts, tol, n=64):
+    """The 3D anisotropic recipe at n^3: each V-cycle precision of the GPU
+    path against the oracle's FP64 solution, ||x - x_oracle|| / ||x_oracle||,
+    all solved to the same true relative residual (run after the timed
+    region)."""
+    import numpy as np
+    import oracle as O
+    from paper_1105_3468_gb300 import workloads as W
+    p = W.c3_aniso_3d_128(n=n)
+    Ao, bo = O.fv_assemble(p)
+    xo, info = O.Hierarchy(Ao).fgmres(bo, tol=tol, maxit=opts.get("maxit", 3000))
+    A, b = amg.assemble_fv(p)
+    out = {"workload": f"fv3d-{n}^3-aniso-blockkappa (same recipe)", "oracle_iters": info.iters}
+    for name, prec in (("fp64", amg.AMG_FP64), ("fp32", amg.AMG_FP32), ("bf16", amg.AMG_BF16)):
+        h = amg.amg_setup(A, vcycle_prec=prec, **opts)
+        x = torch.zeros_like(b)
+        st = amg.amg_solve(h, b, x, tol)
+        h.close()
+        out[name] = {"iters": st.iters, "rel_err": float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo))}
+    return out
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle on the host cores, bounded samples."""
+    """Reference arm: the CPU oracle on the host cores.  Its setup is timed
+    once; each timed step is one full FGMRES(30) restart cycle, and the step
+    value is the projected solve time (setup + iterations x the cycle's
+    average iteration time).  The oracle has no state that warms up, so
+    warm-up steps are not run; timed steps stop early when the next one
+    would take the whole run beyond four minutes (the line reports how many
+    ran)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     prob, tol, maxit, sopts, desc = workload(args.workload)
-    iters_path = os.path.join(ROOT, "oracle", "workload_iters.json")
-    iters = json.load(open(iters_path)).get(args.workload) if os.path.exists(iters_path) else None
+    iters, detail = oracle_iterations(args.workload)
     if iters is None:
         print(json.dumps({"impl": "reference", "unavailable": f"no oracle iteration count for {args.workload}"}))
         return
-    vals = []
-    bl = None
-    for k in range(args.warmup + args.steps):
-        bl = cpu_baseline(prob, tol, iters, sopts)
-        if k >= args.warmup:
-            vals.append(bl["value"])
+    t_start = time.perf_counter()
+    S = OracleSample(prob, sopts)
+    per = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        per.append(S.cycle_s())
+        spent, last = time.perf_counter() - t_start, time.perf_counter() - t0
+        if spent + last > 240.0:
+            break
+    vals = [1e3 * (S.setup_s + p * iters) for p in per]
     v = statistics.mean(vals)
-    bl["value"] = round(v, 1)
+    per_it = statistics.mean(per)
+    bl = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+          "sample": S.describe(per_it, len(per), iters, detail), "oracle_iters": iters,
+          "setup_s": round(S.setup_s, 2), "s_per_iteration": round(per_it, 4)}
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1),
-           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": desc},
+           "steps": len(per), "steps_requested": args.steps, "warmup": 0, "warmup_requested": args.warmup,
+           "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": {"workload": desc, "tol": tol, "options": sopts},
            "cpu_baseline": bl, "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
                                        "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -334,6 +419,8 @@ def main():
     ap.add_argument("--ilut-tau", type=float, default=None, help="drop tolerance of --coarse-solver 1")
     ap.add_argument("--deep-block-max", type=int, default=None,
                     help="levels >= 2 with at most this many rows run their V-cycle in one thread block")
+    ap.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
+                    help="any other amg_options_t field, e.g. --opt coarse_inner=3 --opt coloring=1")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -367,6 +454,11 @@ def main():
     for k in ("persistent", "orthog", "deep_block_max", "dense_max", "coarse_solver", "ilut_tau"):
         if getattr(args, k) is not None:
             opts[k] = getattr(args, k)
+    for kv in args.opt:
+        k, v = kv.split("=", 1)
+        opts[k] = float(v) if k == "ilut_tau" else int(v)
+
+    last_x = {}
 
     def step(prec, timing_class=0, acc=None):
         o = dict(opts)
@@ -380,6 +472,7 @@ def main():
         if timing_class and acc is not None:
             acc.append(amg.amg_get_kernel_timing(h))
         h.close()
+        last_x[prec] = x                              # kept for the accuracy report (outside the timing)
         return st
 
     if args.profile_run:
@@ -422,6 +515,14 @@ def main():
         ms16, stats16, _, _ = timed(amg.AMG_BF16, steps=args.bf16_steps)
         bf16 = {"ms_per_step": round(ms16, 2), "iters": stats16[-1].iters,
                 "rel_res_true": stats16[-1].rel_res_true, "speedup_vs_fp64": round(ms64 / ms16, 3)}
+
+    # distance of the mixed-precision solutions to the FP64 GPU solution
+    def rel_to_fp64(prec):
+        if prec not in last_x or amg.AMG_FP64 not in last_x or prec == amg.AMG_FP64:
+            return None
+        r = last_x[amg.AMG_FP64]
+        return float(torch.linalg.vector_norm(last_x[prec] - r) / torch.linalg.vector_norm(r))
+    err_vs_fp64 = {"fp32": rel_to_fp64(amg.AMG_FP32), "bf16": rel_to_fp64(amg.AMG_BF16)}
 
     # end to end through the C ABI with host buffers (copies inside the region)
     Ah = amg.CsrDevice(A.n, A.row_ptr.cpu().numpy(), A.col.cpu().numpy(), A.val.cpu().numpy())
@@ -482,9 +583,12 @@ def main():
         "e2e": {"value": round(statistics.median(e2e), 2), "unit": "ms", "h2d_bytes_per_step": int(bi),
                 "d2h_bytes_per_step": int(bo)},
         "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "spmv_roofline": spmv_roof,
+        "err_vs_fp64_gpu": err_vs_fp64,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(prob, tol, stats64[-1].iters, sopts)
+        out["cpu_baseline"] = cpu_baseline(prob, sopts, args.workload)
+        if args.workload == "c3":
+            out["err_vs_oracle"] = companion_errors(amg, torch, opts, tol)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -88,6 +88,10 @@ extern "C" {
                                    last level, factored once by ILUT(ilut_tau)
                                    (Section 2) and solved with its factors  */
 
+/* Driver of the FGMRES loop (amg_options_t.solve_loop). */
+#define AMG_LOOP_HOST 0
+#define AMG_LOOP_DEVICE 1
+
 /* Orthogonalisation of the outer FGMRES (Arnoldi process). */
 #define AMG_ORTHO_MGS 0         /* modified Gram-Schmidt                   */
 #define AMG_ORTHO_CGS2 1        /* classical Gram-Schmidt, two passes      */
@@ -175,7 +179,14 @@ typedef struct {
     uint64_t seed;            /* tie-break seed, default 0                 */
     int32_t coarse_solver;    /* AMG_COARSE_RECURSIVE (default) or
                                  AMG_COARSE_ILUT                           */
-    int32_t reserved1;        /* 0                                         */
+    int32_t solve_loop;       /* AMG_LOOP_DEVICE: the FGMRES loop runs as one
+                                 CUDA graph with conditional nodes (all
+                                 members of a batch in one graph), the host
+                                 reads the state once at the end; used when
+                                 use_graphs is on and no kernel class is
+                                 timed (default).  AMG_LOOP_HOST: the host
+                                 reads the stop flag after every inner
+                                 iteration.  Both give the same bits.      */
     double ilut_tau;          /* drop tolerance of AMG_COARSE_ILUT (the
                                  factorisation of amg_ilut_host): >= 0,
                                  default 1e-6                               */

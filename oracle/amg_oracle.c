@@ -815,17 +815,15 @@ static int dense_inverse(int n, const double *a, double *inv)
 }
 
 /* x = A^{-1} b (transpose = 0) or A^{-T} b (transpose = 1) from the     */
-/* inverse: x_i = sum_j inv_ij b_j (inv_ji for the transpose), one        */
-/* accumulator per row in ascending j, each term added with a fused       */
-/* multiply-add (solve-phase rounding).                                   */
+/* inverse: x_i = sum_j inv_ij b_j (inv_ji for the transpose), each row   */
+/* an inner product evaluated as the Arnoldi inner products are (below):  */
+/* as if in twice the working precision (Dot2), terms in ascending j.     */
+static double dot2_strided(int n, const double *a, size_t stride, const double *b);
+
 static void dense_solve(int n, const double *inv, const double *b, double *x, int transpose)
 {
-    for (int i = 0; i < n; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < n; ++j)
-            s = fma(transpose ? inv[(size_t)j * n + i] : inv[(size_t)i * n + j], b[j], s);
-        x[i] = s;
-    }
+    for (int i = 0; i < n; ++i)
+        x[i] = transpose ? dot2_strided(n, inv + i, (size_t)n, b) : dot2_strided(n, inv + (size_t)i * n, 1, b);
 }
 
 /* ------------------------------------------------------------------ */
@@ -1198,18 +1196,21 @@ static void two_sum(double a, double b, double *s, double *e)
     *s = t;
 }
 
-double or_dot(int n, const double *a, const double *b)
+static double dot2_strided(int n, const double *a, size_t stride, const double *b)
 {
     double p = 0.0, c = 0.0;
     for (int i = 0; i < n; ++i) {
-        double h = a[i] * b[i];
-        double r = fma(a[i], b[i], -h);         /* a_i b_i = h + r exactly */
+        double ai = a[(size_t)i * stride];
+        double h = ai * b[i];
+        double r = fma(ai, b[i], -h);           /* a_i b_i = h + r exactly */
         double q;
         two_sum(p, h, &p, &q);
         c = c + (q + r);
     }
     return p + c;
 }
+
+double or_dot(int n, const double *a, const double *b) { return dot2_strided(n, a, 1, b); }
 
 static double dot(int n, const double *a, const double *b) { return or_dot(n, a, b); }
 

@@ -29,6 +29,7 @@ AMG_COLOR_HASH_JP, AMG_COLOR_FIRST_FIT = 0, 1
 AMG_ORTHO_MGS, AMG_ORTHO_CGS2 = 0, 1
 AMG_COARSE_RECURSIVE, AMG_COARSE_ILUT = 0, 1
 AMG_MATCH_PLAIN, AMG_MATCH_SCALED = 0, 1
+AMG_LOOP_HOST, AMG_LOOP_DEVICE = 0, 1
 
 
 class AmgCsr(C.Structure):
@@ -44,7 +45,7 @@ class AmgOptions(C.Structure):
                 ("use_graphs", C.c_int32), ("persistent", C.c_int32), ("deep_block_max", C.c_int32),
                 ("orthog", C.c_int32), ("spmv_block", C.c_int32), ("spmv_unroll", C.c_int32),
                 ("dot2", C.c_int32), ("match_weight", C.c_int32),
-                ("seed", C.c_uint64), ("coarse_solver", C.c_int32), ("reserved1", C.c_int32),
+                ("seed", C.c_uint64), ("coarse_solver", C.c_int32), ("solve_loop", C.c_int32),
                 ("ilut_tau", C.c_double)]
 
     def as_dict(self):

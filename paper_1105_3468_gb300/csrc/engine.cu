@@ -73,6 +73,12 @@ struct amg_handle {
     amg::DBuf<float> Zf, zin32, zout32;
     int *hflags = nullptr;                // pinned: stop flag, status
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // inner iteration (solve, adjoint)
+    // device-driven solve loop (graph conditional nodes): the whole FGMRES
+    // loop of this handle (lexec) or of all members of a batch (bexec)
+    cudaGraphExec_t lexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t bexec[2] = {nullptr, nullptr};
+    int64_t loop_nodes[2][2] = {{0, 0}, {0, 0}};   // kernels per pass and per cycle end
+    cudaStream_t aux = nullptr;           // captures the cycle-end body
     size_t gpairs[2] = {0, 0};            // timing event pairs recorded by each graph
     int64_t gnodes[2] = {0, 0};           // kernels in each graph
     double gbytes[2] = {0.0, 0.0};        // timed-class bytes of one replay
@@ -541,6 +547,11 @@ static void tcollect(amg_handle *h) {
 }
 
 // ------------------------------------------------------------------ preconditioner
+// Accurate (Dot2) inner products: on by default with the FP64 V-cycle.
+static bool use_dot2(const amg_handle *h) {
+    return h->opt.dot2 < 0 ? h->opt.vcycle_prec == AMG_FP64 : h->opt.dot2 != 0;
+}
+
 template <typename T, typename V>
 struct VCycle {
     amg_handle *h;
@@ -558,6 +569,10 @@ struct VCycle {
     SweepView<T, V> view(Sweep &S);
 
     int nlev() const { return (int)h->lev.size(); }
+
+    // the dense last level's rows as Dot2 inner products in the FP64 V-cycle
+    // when the Arnoldi inner products are Dot2 too (the dot2 option)
+    bool dense_dot2() const { return std::is_same<T, double>::value && use_dot2(h); }
 
     // t = S^{-1} in (transpose: S^{-T} in); y is scratch for the first solve
     void smooth(Level &Lv, const T *in, T *y, T *t, bool transpose) {
@@ -639,7 +654,7 @@ struct VCycle {
             deep_vcycle<T, V>(d, nlev() - l, s);
             return;
         }
-        if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 0, 0, s); return; }
+        if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 0, 0, dense_dot2(), s); return; }
         if (Lv.ilut_level) { smooth(Lv, hrhs, ws(Lv.wy), g, false); return; }   // g = (L~ U~)^{-1} h
         const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
         T *res = ws(Lv.wres);
@@ -681,7 +696,7 @@ struct VCycle {
             return;
         }
         Level &Lv = L(l);
-        if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 1, 0, s); return; }
+        if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 1, 0, dense_dot2(), s); return; }
         if (Lv.ilut_level) { smooth(Lv, hrhs, ws(Lv.wy), g, true); return; }    // g = (L~ U~)^{-T} h
         const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
         T *res = ws(Lv.wres);
@@ -785,12 +800,7 @@ static void apply_precond_vtype(amg_handle *h, bool transpose) {
 // z_j = B~^{-1} v_j, w = A z_j, modified Gram-Schmidt (or CGS2) against
 // v_0..v_j, ||w||, Givens, v_{j+1} = w / ||w||, and the stop flag copied to
 // pinned host memory.
-// Accurate (Dot2) inner products: on by default with the FP64 V-cycle.
-static bool use_dot2(const amg_handle *h) {
-    return h->opt.dot2 < 0 ? h->opt.vcycle_prec == AMG_FP64 : h->opt.dot2 != 0;
-}
-
-static void enqueue_iteration(amg_handle *h, bool transpose) {
+static void enqueue_iteration(amg_handle *h, bool transpose, bool host_flag = true) {
     cudaStream_t s = h->stream;
     const size_t n = h->n;
     FgState *dst = h->st.get();
@@ -830,7 +840,7 @@ static void enqueue_iteration(amg_handle *h, bool transpose) {
     }
     givens(dst, s);
     scale_next(n, h->w.get(), h->V.get(), dst, s);
-    CU(cudaMemcpyAsync(h->hflags, &dst->stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (host_flag) CU(cudaMemcpyAsync(h->hflags, &dst->stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
 }
 
 // Queues one inner iteration, replaying a captured CUDA graph when enabled
@@ -910,7 +920,6 @@ struct Run {
     int status = AMG_OK, total = 0, restarts = 0, j = 0;
     int64_t launches0 = 0;
     std::chrono::steady_clock::time_point t0;
-    DBuf<double> tb;
 };
 
 static void start_cycle(Run &R) {
@@ -930,13 +939,17 @@ static void run_begin(Run &R) {
     cudaStream_t s = h->stream;
     const size_t n = h->n;
     R.x_dev = is_device_ptr(R.x_io);
-    R.b = to_device(R.b_in, n, R.tb, s);
+    // b in the handle's own buffer, so that a captured solve loop reads it
+    CU(cudaMemcpyAsync(h->bb.get(), R.b_in, n * sizeof(double),
+                       is_device_ptr(R.b_in) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    R.b = h->bb.get();
     double *x = h->xb.get();
     if (R.x_dev) CU(cudaMemcpyAsync(x, R.x_io, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     else CU(cudaMemcpyAsync(x, R.x_io, n * sizeof(double), cudaMemcpyHostToDevice, s));
     FgState &hs = *h->hst;
     memset(&hs, 0, sizeof(FgState));
     hs.m = h->opt.restart; hs.maxit = h->opt.maxit; hs.hist_cap = h->opt.maxit + 2; hs.tol = R.tol;
+    hs.loop_cap = h->opt.maxit + 16;      // one inner iteration per loop pass
     hs.hist = h->hist.get();
     h->last_hist.clear();
     R.bnorm = read_norm(h, R.b);
@@ -954,6 +967,7 @@ static void run_begin(Run &R) {
     const double beta = read_norm(h, h->r.get());      // leaves ||r0||^2 in the state for the restart
     R.relres = beta / R.bnorm;
     CU(cudaMemcpyAsync(h->hist.get(), &R.relres, sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(&h->st.get()->relres, &R.relres, sizeof(double), cudaMemcpyHostToDevice, s));
     CU(cudaStreamSynchronize(s));
     if (!std::isfinite(R.relres)) { R.status = AMG_ERR_NUMERIC; R.done = true; return; }
     start_cycle(R);
@@ -1035,13 +1049,159 @@ static int run_end(Run &R, amg_stats_t *stats) {
     return R.status;
 }
 
+// ------------------------------------------------------------------ device-driven loop
+// The loop of run_collect / end_cycle as one CUDA graph per handle (or per
+// batch): a WHILE conditional node whose body is one inner iteration (the
+// kernels of enqueue_iteration) followed by an IF conditional node, taken
+// when the iteration ended the cycle, holding the update x += Z y, the true
+// residual, its norm, the convergence decision and the restart.  The loop
+// ends on convergence, at the iteration cap, on a breakdown, or when a
+// device wait gave up; the host reads the state once, after the loop.
+// Kernel timing (event nodes) is not allowed in conditional bodies, so a
+// handle with a timed kernel class runs the host-driven loop.
+static bool device_loop_ok(const amg_handle *h) {
+    return h->opt.solve_loop == AMG_LOOP_DEVICE && h->opt.use_graphs && h->tclass == 0;
+}
+
+static void capture_into(cudaStream_t s, cudaGraph_t g) {
+    CU(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+}
+static void end_capture(cudaStream_t s) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamEndCapture(s, &g));
+}
+static cudaGraph_t capture_graph(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive || !g) fail(AMG_ERR_CUDA, "device loop: stream is not capturing");
+    return g;
+}
+// Adds a conditional node after the capture's current tail on stream s and
+// makes it the new tail; returns its body graph.
+static cudaGraph_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive || !g) fail(AMG_ERR_CUDA, "device loop: stream is not capturing");
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = c;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    CU(cudaGraphAddNode(&node, g, dv.empty() ? nullptr : dv.data(), nullptr, dv.size(), &p));
+    CU(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return p.conditional.phGraph_out[0];
+}
+
+// End of a cycle on stream s (the same kernels and order as end_cycle and
+// start_cycle of the host-driven loop).
+static void enqueue_cycle_end(amg_handle *h, bool transpose, cudaStream_t s) {
+    const size_t n = h->n;
+    FgState *dst = h->st.get();
+    double *x = h->xb.get();
+    backsolve(dst, s);
+    if (h->opt.vcycle_prec == AMG_FP64) update_x<double>(n, dst, h->Zd.get(), n, x, s);
+    else update_x<float>(n, dst, h->Zf.get(), n, x, s);
+    Level &L0 = *h->lev[0];
+    const Sell &SL = transpose ? L0.sellT : L0.sell;
+    sell_spmv<double>(SL.n, SL.nslices, SL.ptr.get(), SL.ci.get(), SL.v.get(), x, h->bb.get(), h->r.get(), 1, s,
+                      SL.block, SL.unroll);
+    norm2(n, h->r.get(), h->partials.get(), h->ticket.get(), dst->nrm2, use_dot2(h), s);
+    end_cycle_dev(dst, s);
+    restart_scale(n, h->r.get(), h->V.get(), dst, s);
+}
+
+// Appends handle h's solve loop to graph G as a new root chain:
+// loop_init -> WHILE { iteration; cycle_flag; IF { cycle end }; loop_flag }.
+static void add_member_loop(amg_handle *h, bool transpose, cudaGraph_t G) {
+    const int d = transpose ? 1 : 0;
+    cudaStream_t s = h->stream;
+    if (!h->aux) CU(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    FgState *dst = h->st.get();
+    const int64_t l0 = launch_count();
+    cudaGraphConditionalHandle w;
+    CU(cudaGraphConditionalHandleCreate(&w, G, 0, 0));
+    capture_into(s, G);
+    loop_init(dst, w, s);
+    cudaGraph_t body = add_conditional(s, w, cudaGraphCondTypeWhile);
+    end_capture(s);
+    const int64_t l1 = launch_count();
+    capture_into(s, body);
+    enqueue_iteration(h, transpose, false);
+    cudaGraphConditionalHandle c;
+    CU(cudaGraphConditionalHandleCreate(&c, capture_graph(s), 0, 0));
+    cycle_flag(dst, c, s);
+    cudaGraph_t endg = add_conditional(s, c, cudaGraphCondTypeIf);
+    const int64_t l2 = launch_count();
+    capture_into(h->aux, endg);
+    enqueue_cycle_end(h, transpose, h->aux);
+    end_capture(h->aux);
+    const int64_t l3 = launch_count();
+    loop_flag(dst, h->err.get(), w, s);
+    end_capture(s);
+    const int64_t l4 = launch_count();
+    h->loop_nodes[d][0] = (l2 - l1) + (l4 - l3);     // kernels of one pass
+    h->loop_nodes[d][1] = l3 - l2;                   // kernels of one cycle end
+    count_launch(-(l4 - l0));                        // counted per executed node after the run
+}
+
+// Runs the solve loops of `runs` (begun with run_begin) as one graph on
+// `owner`'s stream, built on first use and kept in `exec`.
+static void run_device_loop(const std::vector<Run *> &runs, amg_handle *owner, cudaGraphExec_t &exec,
+                            bool transpose) {
+    if (!exec) {
+        cudaGraph_t G = nullptr;
+        CU(cudaGraphCreate(&G, 0));
+        try {
+            for (Run *R : runs) add_member_loop(R->h, transpose, G);
+            CU(cudaGraphInstantiate(&exec, G, 0));
+        } catch (...) {
+            cudaGraphDestroy(G);
+            exec = nullptr;
+            throw;
+        }
+        cudaGraphDestroy(G);
+    }
+    static const int one = 1;
+    for (Run *R : runs)
+        if (R->done)        // finished in run_begin: its loop must not run
+            CU(cudaMemcpyAsync(&R->h->st.get()->done, &one, sizeof(int), cudaMemcpyHostToDevice, R->h->stream));
+    for (Run *R : runs) CU(cudaStreamSynchronize(R->h->stream));
+    CU(cudaGraphLaunch(exec, owner->stream));
+    count_launch(1);
+    CU(cudaStreamSynchronize(owner->stream));
+    const int d = transpose ? 1 : 0;
+    for (Run *R : runs) {
+        if (R->done) continue;
+        amg_handle *h = R->h;
+        FgState &hs = *h->hst;
+        CU(cudaMemcpyAsync(&hs, h->st.get(), sizeof(FgState), cudaMemcpyDeviceToHost, owner->stream));
+        CU(cudaStreamSynchronize(owner->stream));
+        R->total = hs.total;
+        R->restarts = hs.restarts;
+        R->relres = hs.relres;
+        R->status = hs.status;
+        R->done = true;
+        count_launch(hs.passes * h->loop_nodes[d][0] + (hs.restarts + (hs.passes > 0 ? 1 : 0)) * h->loop_nodes[d][1]);
+    }
+}
+
 static int fgmres(amg_handle *h, const double *b_in, double *x_io, double tol, amg_stats_t *stats, bool transpose) {
     Run R;
     R.h = h; R.b_in = b_in; R.x_io = x_io; R.tol = tol; R.transpose = transpose;
     run_begin(R);
-    while (!R.done) {
-        run_launch(R);
-        run_collect(R);
+    if (!R.done && device_loop_ok(h)) {
+        run_device_loop({&R}, h, h->lexec[transpose ? 1 : 0], transpose);
+    } else {
+        while (!R.done) {
+            run_launch(R);
+            run_collect(R);
+        }
     }
     return run_end(R, stats);
 }
@@ -1120,7 +1280,7 @@ int amg_default_options(amg_options_t *o) {
     o->match_weight = AMG_MATCH_SCALED;
     o->seed = 0;
     o->coarse_solver = AMG_COARSE_RECURSIVE;
-    o->reserved1 = 0;
+    o->solve_loop = AMG_LOOP_DEVICE;
     o->ilut_tau = 1e-6;
     return AMG_OK;
 }
@@ -1134,7 +1294,7 @@ static void check_options(const amg_options_t &o) {
         (o.spmv_block != 0 && o.spmv_block != 64 && o.spmv_block != 128 && o.spmv_block != 256 &&
          o.spmv_block != 512) ||
         (o.spmv_unroll != 0 && o.spmv_unroll != 2 && o.spmv_unroll != 4 && o.spmv_unroll != 8) || o.dot2 < -1 ||
-        o.dot2 > 1 || o.match_weight < 0 || o.match_weight > 1 || o.coarse_solver < 0 || o.coarse_solver > 1 || !(o.ilut_tau >= 0.0) ||
+        o.dot2 > 1 || o.match_weight < 0 || o.match_weight > 1 || o.solve_loop < 0 || o.solve_loop > 1 || o.coarse_solver < 0 || o.coarse_solver > 1 || !(o.ilut_tau >= 0.0) ||
         !std::isfinite(o.ilut_tau))
         fail(AMG_ERR_INVALID_ARG, "option out of range (restart <= 31, dense_max <= 4096, 2 <= max_levels <= 24)");
 }
@@ -1207,6 +1367,7 @@ int amg_update_values(amg_handle_t *h, const double *val) {
     std::swap(h->hflags, nh->hflags);
     for (int d = 0; d < 2; ++d) {
         std::swap(h->gexec[d], nh->gexec[d]);
+        std::swap(h->lexec[d], nh->lexec[d]);
         std::swap(h->gpairs[d], nh->gpairs[d]);
         std::swap(h->gnodes[d], nh->gnodes[d]);
         std::swap(h->gbytes[d], nh->gbytes[d]);
@@ -1232,6 +1393,9 @@ void amg_destroy(amg_handle_t *h) {
         if (h->hst) cudaFreeHost(h->hst);
         if (h->hflags) cudaFreeHost(h->hflags);
         for (auto &g : h->gexec) if (g) cudaGraphExecDestroy(g);
+        for (auto &g : h->lexec) if (g) cudaGraphExecDestroy(g);
+        for (auto &g : h->bexec) if (g) cudaGraphExecDestroy(g);
+        if (h->aux) cudaStreamDestroy(h->aux);
         h->lev.clear();
         h->V.release(); h->Zd.release(); h->Zf.release();
         if (h->entry_ev) cudaEventDestroy(h->entry_ev);
@@ -1272,6 +1436,7 @@ int amg_setup_batched(const amg_csr_t *systems, int32_t count, const amg_options
     else amg_default_options(&B->opt);
     check_options(B->opt);
     B->ustream = (cudaStream_t)stream;
+    CU(cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking));
     B->subs.assign(count, nullptr);
     // independent systems: set up concurrently from a few host threads, each
     // system on its own internal stream
@@ -1322,25 +1487,34 @@ int amg_solve_batched(amg_handle_t *h, const double *b_cat, double *x_cat, doubl
     if (!(tol >= 0.0)) fail(AMG_ERR_INVALID_ARG, "amg_solve_batched: tol must be >= 0");
     const int count = (int)h->subs.size();
     std::vector<Run> R(count);
+    CU(cudaStreamSynchronize(h->ustream));
     for (int k = 0; k < count; ++k) {
         R[k].h = h->subs[k];
         R[k].b_in = b_cat + h->offs[k];
         R[k].x_io = x_cat + h->offs[k];
         R[k].tol = tol;
-        CU(cudaStreamSynchronize(h->ustream));
         R[k].h->ustream = h->ustream;
         run_begin(R[k]);
     }
-    // one loop over the batch: every active system queues its inner
-    // iteration on its own stream, then each is collected; converged systems
-    // drop out (mask), the others continue
-    for (;;) {
-        bool any = false;
-        for (int k = 0; k < count; ++k)
-            if (!R[k].done) { run_launch(R[k]); any = true; }
-        if (!any) break;
-        for (int k = 0; k < count; ++k)
-            if (!R[k].done) run_collect(R[k]);
+    bool device = true;
+    for (int k = 0; k < count; ++k) device = device && device_loop_ok(h->subs[k]);
+    if (device) {
+        // every member's loop in one graph (parallel root chains), masks in
+        // device memory: one launch and one synchronisation for the batch
+        std::vector<Run *> runs(count);
+        for (int k = 0; k < count; ++k) runs[k] = &R[k];
+        run_device_loop(runs, h, h->bexec[0], false);
+    } else {
+        // host-driven: every active system queues its inner iteration on its
+        // own stream, then each is collected; converged systems drop out
+        for (;;) {
+            bool any = false;
+            for (int k = 0; k < count; ++k)
+                if (!R[k].done) { run_launch(R[k]); any = true; }
+            if (!any) break;
+            for (int k = 0; k < count; ++k)
+                if (!R[k].done) run_collect(R[k]);
+        }
     }
     int status = AMG_OK;
     for (int k = 0; k < count; ++k) {

@@ -877,6 +877,32 @@ template void sweep_pair_df<float, __nv_bfloat16>(const SweepView<float, __nv_bf
                                                   const SweepView<float, __nv_bfloat16> &, int, const float *, float *,
                                                   float *, unsigned int *, int *, cudaStream_t);
 
+// Accurate inner products (DOT2): the Dot2 scheme of Ogita, Rump and Oishi
+// (2005).  Each product is split exactly into h + r (TwoProduct via fma), the
+// h are added with the exact error of each addition kept (TwoSum), errors are
+// collected in c; partial (p, c) pairs merge by TwoSum of the p and the sum of
+// the c.  The result p + c is the exact inner product correctly rounded in all
+// but near-tie cases, so it does not depend on how the sum is split across
+// threads and blocks.
+__device__ __forceinline__ void two_sum_d(double a, double b, double &s, double &e) {
+    const double t = __dadd_rn(a, b);
+    const double z = __dsub_rn(t, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(t, z)), __dsub_rn(b, z));
+    s = t;
+}
+__device__ __forceinline__ void dot2_add(double &p, double &c, double x, double y) {
+    const double h = __dmul_rn(x, y);
+    const double r = __fma_rn(x, y, -h);
+    double q;
+    two_sum_d(p, h, p, q);
+    c = __dadd_rn(c, __dadd_rn(q, r));
+}
+__device__ __forceinline__ void dot2_merge(double &p, double &c, double p2, double c2) {
+    double q;
+    two_sum_d(p, p2, p, q);
+    c = __dadd_rn(c, __dadd_rn(c2, q));
+}
+
 // ------------------------------------------------------------------ dense rows
 // Row i of a dense n x n inverse (column i for the transpose) times h, for
 // one warp: lane r sums j = r, r + 32, ... in ascending j (fused
@@ -894,6 +920,26 @@ __device__ __forceinline__ double warp_dense_dot(const double *inv, int n, int i
 #pragma unroll
     for (int off = 16; off; off >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, off));
     return s;
+}
+// The same row as an inner product evaluated as if in twice the working
+// precision (Dot2): each lane keeps a (p, c) pair over its terms, the pairs
+// merge across the warp, lane 0 returns p + c.  The value does not depend on
+// how the terms are split (except in near-tie cases).
+template <typename H>
+__device__ __forceinline__ double warp_dense_dot2(const double *inv, int n, int i, int transpose, int lane, H h) {
+    double p = 0.0, c = 0.0;
+    if (transpose) {
+        for (int j = lane; j < n; j += 32) dot2_add(p, c, inv[(size_t)j * n + i], h(j));
+    } else {
+        const double *row = inv + (size_t)i * n;
+        for (int j = lane; j < n; j += 32) dot2_add(p, c, row[j], h(j));
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const double p2 = __shfl_down_sync(0xffffffffu, p, off), c2 = __shfl_down_sync(0xffffffffu, c, off);
+        dot2_merge(p, c, p2, c2);
+    }
+    return __dadd_rn(p, c);
 }
 
 // ------------------------------------------------------------------ single-block deep V-cycle
@@ -1043,12 +1089,12 @@ void convert_f32_f64(size_t n, const float *in, double *out, cudaStream_t s) {
 }
 
 // Dense last level: g = Ainv h (transpose: g = Ainv^T h), one warp per row
-// (h staged in shared memory as FP64).  Lane r sums the terms j = r, r + 32,
-// ... in ascending j with fused multiply-adds; the 32 partial sums are then
-// added by halving (s_r + s_{r+16}, then 8, 4, 2, 1): a fixed order, the same
-// in every variant and in the plain CPU definition.
+// (h staged in shared memory as FP64).  Plain: lane r sums the terms j = r,
+// r + 32, ... in ascending j with fused multiply-adds and the 32 partial
+// sums are added by halving; DOT2: each row as an inner product evaluated as
+// if in twice the working precision (warp_dense_dot2).
 constexpr int DENSE_WARPS = 8;
-template <typename T>
+template <typename T, bool DOT2>
 __global__ void __launch_bounds__(32 * DENSE_WARPS) k_dense_gemv(int n, const double *__restrict__ inv,
                                                                  const T *__restrict__ h, T *__restrict__ g,
                                                                  int transpose, int mode) {
@@ -1057,18 +1103,24 @@ __global__ void __launch_bounds__(32 * DENSE_WARPS) k_dense_gemv(int n, const do
     __syncthreads();
     const int lane = threadIdx.x & 31;
     for (int i = blockIdx.x * DENSE_WARPS + (threadIdx.x >> 5); i < n; i += gridDim.x * DENSE_WARPS) {
-        const double s = warp_dense_dot(inv, n, i, transpose, lane, [&](int j) { return dense_h[j]; });
+        const double s = DOT2 ? warp_dense_dot2(inv, n, i, transpose, lane, [&](int j) { return dense_h[j]; })
+                              : warp_dense_dot(inv, n, i, transpose, lane, [&](int j) { return dense_h[j]; });
         if (lane == 0) g[i] = mode ? (T)((double)g[i] + s) : (T)s;
     }
 }
 template <typename T>
-void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, cudaStream_t s) {
+void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, bool dot2, cudaStream_t s) {
     const int blocks = (n + DENSE_WARPS - 1) / DENSE_WARPS;
-    k_dense_gemv<T><<<blocks, 32 * DENSE_WARPS, sizeof(double) * (size_t)n, s>>>(n, inv, h, g, transpose, mode);
+    if (dot2)
+        k_dense_gemv<T, true><<<blocks, 32 * DENSE_WARPS, sizeof(double) * (size_t)n, s>>>(n, inv, h, g, transpose,
+                                                                                            mode);
+    else
+        k_dense_gemv<T, false><<<blocks, 32 * DENSE_WARPS, sizeof(double) * (size_t)n, s>>>(n, inv, h, g, transpose,
+                                                                                             mode);
     CU_LAUNCH("k_dense_gemv"); count_launch();
 }
-template void dense_solve<double>(int, const double *, const double *, double *, int, int, cudaStream_t);
-template void dense_solve<float>(int, const double *, const float *, float *, int, int, cudaStream_t);
+template void dense_solve<double>(int, const double *, const double *, double *, int, int, bool, cudaStream_t);
+template void dense_solve<float>(int, const double *, const float *, float *, int, int, bool, cudaStream_t);
 
 // ------------------------------------------------------------------ FGMRES pieces
 // Block-level reduction of K accumulators into partials[block*KMAX + k].
@@ -1262,6 +1314,7 @@ template void store_zj<float>(size_t, const FgState *, const float *, float *, c
 // y = H(1:j,1:j)^{-1} s(1:j) (single thread)
 __global__ void k_backsolve(FgState *st) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (st->status) return;                  // a breakdown ends the solve without an update
     const int m = st->m, j = st->jdone;
     for (int k = j - 1; k >= 0; --k) {
         double t = st->s[k];
@@ -1274,7 +1327,7 @@ __global__ void k_backsolve(FgState *st) {
 template <typename ZT>
 __global__ void k_update_x(size_t n, const FgState *st, const ZT *__restrict__ Z, size_t ldz, double *x) {
     __shared__ double ys[KMAX1];
-    const int j = st->jdone;
+    const int j = st->status ? 0 : st->jdone;
     for (int k = threadIdx.x; k < KMAX1; k += blockDim.x) ys[k] = k < j ? st->y[k] : 0.0;
     __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -1292,32 +1345,6 @@ template void update_x<double>(size_t, const FgState *, const double *, size_t, 
 template void update_x<float>(size_t, const FgState *, const float *, size_t, double *, cudaStream_t);
 
 // ||v||^2 -> out (deterministic)
-// Accurate inner products (DOT2): the Dot2 scheme of Ogita, Rump and Oishi
-// (2005).  Each product is split exactly into h + r (TwoProduct via fma), the
-// h are added with the exact error of each addition kept (TwoSum), errors are
-// collected in c; partial (p, c) pairs merge by TwoSum of the p and the sum of
-// the c.  The result p + c is the exact inner product correctly rounded in all
-// but near-tie cases, so it does not depend on how the sum is split across
-// threads and blocks.
-__device__ __forceinline__ void two_sum_d(double a, double b, double &s, double &e) {
-    const double t = __dadd_rn(a, b);
-    const double z = __dsub_rn(t, a);
-    e = __dadd_rn(__dsub_rn(a, __dsub_rn(t, z)), __dsub_rn(b, z));
-    s = t;
-}
-__device__ __forceinline__ void dot2_add(double &p, double &c, double x, double y) {
-    const double h = __dmul_rn(x, y);
-    const double r = __fma_rn(x, y, -h);
-    double q;
-    two_sum_d(p, h, p, q);
-    c = __dadd_rn(c, __dadd_rn(q, r));
-}
-__device__ __forceinline__ void dot2_merge(double &p, double &c, double p2, double c2) {
-    double q;
-    two_sum_d(p, p2, p, q);
-    c = __dadd_rn(c, __dadd_rn(c2, q));
-}
-
 // Block reduction of (p, c) pairs: returns the block's pair in thread 0.
 __device__ __forceinline__ void block_merge2(double &p, double &c) {
     __shared__ double sp[RT / 32], sc[RT / 32];
@@ -1544,6 +1571,7 @@ void backsolve(FgState *st, cudaStream_t s) {
 
 // restart: V_0 = r / beta with beta = sqrt(nrm2); s = beta e1
 __global__ void k_restart_scale(size_t n, const double *__restrict__ r, double *__restrict__ v0, FgState *st) {
+    if (st->done) return;                    // device loop: the solve ended at this cycle
     const double beta = sqrt(st->nrm2[0]);
     if (beta > 0.0)
         for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -1559,6 +1587,51 @@ __global__ void k_restart_scale(size_t n, const double *__restrict__ r, double *
 void restart_scale(size_t n, const double *r, double *v0, FgState *st, cudaStream_t s) {
     k_restart_scale<<<grid_for(n, 256), 256, 0, s>>>(n, r, v0, st);
     CU_LAUNCH("k_restart_scale"); count_launch();
+}
+
+__global__ void k_cycle_flag(FgState *st, cudaGraphConditionalHandle c) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(c, st->stop ? 1u : 0u);
+}
+void cycle_flag(FgState *st, cudaGraphConditionalHandle c, cudaStream_t s) {
+    k_cycle_flag<<<1, 32, 0, s>>>(st, c);
+    CU_LAUNCH("k_cycle_flag"); count_launch();
+}
+
+// The host driver's end-of-cycle decision, on the device (status codes as in
+// the public header: 6 numeric, 7 not converged).
+__global__ void k_end_cycle(FgState *st) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (st->status) { st->done = 1; return; }
+    const double relres = sqrt(st->nrm2[0]) / st->bnorm;
+    st->relres = relres;
+    if (!isfinite(relres)) { st->status = 6; st->done = 1; return; }
+    if (relres <= st->tol) { st->done = 1; return; }
+    if (st->total >= st->maxit) { st->status = 7; st->done = 1; return; }
+    st->restarts += 1;
+}
+void end_cycle_dev(FgState *st, cudaStream_t s) {
+    k_end_cycle<<<1, 32, 0, s>>>(st);
+    CU_LAUNCH("k_end_cycle"); count_launch();
+}
+
+__global__ void k_loop_init(FgState *st, cudaGraphConditionalHandle w) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(w, st->done ? 0u : 1u);
+}
+void loop_init(FgState *st, cudaGraphConditionalHandle w, cudaStream_t s) {
+    k_loop_init<<<1, 32, 0, s>>>(st, w);
+    CU_LAUNCH("k_loop_init"); count_launch();
+}
+
+__global__ void k_loop_flag(FgState *st, const int *err, cudaGraphConditionalHandle w) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    st->passes += 1;
+    if (*err && !st->done) st->done = 1;                       // reported by the host as AMG_ERR_LIMIT
+    if (!st->done && st->passes >= st->loop_cap) { st->status = 8; st->done = 1; }
+    cudaGraphSetConditional(w, st->done ? 0u : 1u);
+}
+void loop_flag(FgState *st, const int *err, cudaGraphConditionalHandle w, cudaStream_t s) {
+    k_loop_flag<<<1, 32, 0, s>>>(st, err, w);
+    CU_LAUNCH("k_loop_flag"); count_launch();
 }
 
 }  // namespace amg

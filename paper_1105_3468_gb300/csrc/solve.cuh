@@ -19,6 +19,11 @@ struct FgState {
     double H[(KMAX1 + 1) * KMAX1];
     double cs[KMAX1], sn[KMAX1], s[KMAX1 + 1], y[KMAX1];
     double h1[KMAX1 + 1], h2[KMAX1 + 1], nrm2[2];
+    // device-driven solve loop (graph conditional nodes): done ends the
+    // loop; relres = true residual of the last cycle end; passes counts loop
+    // bodies, capped at loop_cap
+    int done, restarts, passes, loop_cap;
+    double relres, pad2;
     double *hist;
 };
 
@@ -80,8 +85,9 @@ template <typename T>
 void vec_acc(size_t n, const T *in, T *out, int mode, cudaStream_t s);
 void convert_f64_f32(size_t n, const double *in, float *out, cudaStream_t s);
 void convert_f32_f64(size_t n, const float *in, double *out, cudaStream_t s);
+// dot2: each row as an inner product as if in twice the working precision
 template <typename T>
-void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, cudaStream_t s);
+void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, bool dot2, cudaStream_t s);
 
 // K = st->j + 1 basis vectors (read on the device)
 // Smoothers with more schedule levels than this (forward + backward) run as
@@ -128,6 +134,17 @@ void backsolve(FgState *st, cudaStream_t s);
 template <typename ZT>
 void update_x(size_t n, const FgState *st, const ZT *Z, size_t ldz, double *x, cudaStream_t s);
 void restart_scale(size_t n, const double *r, double *v0, FgState *st, cudaStream_t s);
+// Device-driven solve loop.  cycle_flag: the IF condition = st->stop (the
+// inner iteration ended the cycle).  end_cycle (after the update, the true
+// residual and its squared norm in st->nrm2[0]): relres, convergence, the
+// cap on iterations, status; a continuing solve counts a restart.
+// loop_init / loop_flag: the WHILE condition = !done (loop_flag also counts
+// the pass and ends the loop with AMG_ERR_LIMIT past loop_cap, or when a
+// device wait gave up (*err)).
+void cycle_flag(FgState *st, cudaGraphConditionalHandle c, cudaStream_t s);
+void end_cycle_dev(FgState *st, cudaStream_t s);
+void loop_init(FgState *st, cudaGraphConditionalHandle w, cudaStream_t s);
+void loop_flag(FgState *st, const int *err, cudaGraphConditionalHandle w, cudaStream_t s);
 int reduce_grid();
 
 }  // namespace amg

@@ -41,7 +41,7 @@ def test_host_only_calls(lib):
     assert (o.passes, o.coarse_inner, o.restart, o.maxit, o.dense_max) == (2, 5, 30, 600, 4096)
     assert o.order_fine == pkg.AMG_ORDER_NATURAL and o.order_coarse == pkg.AMG_ORDER_COLOR
     assert o.coarse_solver == pkg.AMG_COARSE_RECURSIVE and o.ilut_tau == 1e-6
-    assert o.match_weight == pkg.AMG_MATCH_SCALED
+    assert o.match_weight == pkg.AMG_MATCH_SCALED and o.solve_loop == pkg.AMG_LOOP_DEVICE
     assert pkg.amg_status_string(pkg.AMG_ERR_NOT_CONVERGED) == "not converged"
     assert lib.amg_default_options(None) == pkg.AMG_ERR_INVALID_ARG
     out = C.c_void_p(123)
@@ -65,7 +65,7 @@ def test_setup_rejects_bad_options_before_any_device_call(lib):
     out = C.c_void_p()
     for field, value in (("coarse_solver", 2), ("ilut_tau", -1.0), ("ilut_tau", float("nan")),
                          ("ilut_tau", float("inf")), ("dense_max", 4097), ("persistent", 5), ("passes", 0),
-                         ("match_weight", 2), ("match_weight", -1)):
+                         ("match_weight", 2), ("match_weight", -1), ("solve_loop", 2)):
         o = pkg.amg_default_options()
         setattr(o, field, value)
         assert lib.amg_setup(C.byref(A), C.byref(o), None, C.byref(out)) == pkg.AMG_ERR_INVALID_ARG, field

@@ -59,10 +59,13 @@ def _fd_instance():
 def test_logkappa_gradient_fd_16(env):
     """Gradient with respect to per-cell log kappa on the 16^2 instance:
     against the oracle's dense adjoint gradient (1e-6 relative per cell), and
-    against central differences (h = 1e-6 in log kappa) of the loss evaluated
-    through the library's forward solve at tol 1e-13, on every cell: the
-    difference is at most 1e-6 of the largest gradient component (truncation
-    error O(h^2) and the solver's 1e-13 are both far below that bar)."""
+    against central differences of the loss evaluated through the library's
+    assembly and forward solve (tol 1e-13), on every cell.  With the step
+    h = 1e-3 the difference is at most 1e-6 of the largest gradient
+    component (truncation O(h^2) and rounding are both below it).  With the
+    step h = 1e-6 the FP64 rounding of the loss, divided by 2h, dominates:
+    exact dense solves already leave 1.3e-4 of max |g| on this instance
+    (kappa contrast 1e8), so the bar there is 5e-4."""
     amg, O, torch = env
     prob, xt = _fd_instance()
     logk = torch.tensor(np.log(prob.kx), device="cuda", requires_grad=True)
@@ -80,7 +83,6 @@ def test_logkappa_gradient_fd_16(env):
     gref = gx + gy
     scale = np.abs(gref).max()
     assert np.allclose(g, gref, rtol=1e-6, atol=1e-8 * scale)
-    h = 1e-6
     lk = np.log(prob.kx)
 
     def L(v):
@@ -89,14 +91,15 @@ def test_logkappa_gradient_fd_16(env):
         assert st.status == 0
         return float(((xx - xtd) ** 2).sum())
 
-    fd = np.zeros(prob.n)
-    for c in range(prob.n):
-        e = np.zeros(prob.n)
-        e[c] = h
-        fd[c] = (L(lk + e) - L(lk - e)) / (2 * h)
-    err = np.abs(g - fd).max() / scale
-    print(f"16^2 log-kappa gradient vs central differences: max |g - fd| / max |g| = {err:.2e}")
-    assert err <= 1e-6
+    for h, bar in ((1e-3, 1e-6), (1e-6, 5e-4)):
+        fd = np.zeros(prob.n)
+        for c in range(prob.n):
+            e = np.zeros(prob.n)
+            e[c] = h
+            fd[c] = (L(lk + e) - L(lk - e)) / (2 * h)
+        err = np.abs(g - fd).max() / scale
+        print(f"16^2 log-kappa gradient vs central differences, h = {h:g}: max |g - fd| / max |g| = {err:.2e}")
+        assert err <= bar
 
 
 def test_fv_logk_assembly_and_iso_gradient(env):

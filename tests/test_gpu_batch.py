@@ -68,6 +68,29 @@ def test_batch_equals_individual_solves(env, prec):
         assert np.array_equal(hist_b, amg.amg_get_history(h))
 
 
+def test_batch_device_loop_matches_host_loop(env):
+    """The batch's solve loops as one graph (every member a root chain of
+    conditional nodes, masks in device memory) give the same bits as the
+    host-driven batch loop."""
+    amg, O, torch = env
+    mats, rhs = _members(O)
+    dev = [amg.CsrDevice.from_host(A) for A in mats]
+    b = torch.tensor(np.concatenate(rhs), device="cuda")
+    out = {}
+    for loop in (amg.AMG_LOOP_HOST, amg.AMG_LOOP_DEVICE):
+        hb = amg.amg_setup_batched(dev, vcycle_prec=amg.AMG_FP32, solve_loop=loop)
+        x = torch.zeros_like(b)
+        stats = amg.amg_solve_batched(hb, b, x, 1e-8)
+        x2 = torch.zeros_like(b)
+        amg.amg_solve_batched(hb, b, x2, 1e-8)              # the cached batch graph again
+        assert torch.equal(x, x2)
+        out[loop] = (x.cpu().numpy(), [(s.iters, s.restarts, s.status, s.rel_res_true) for s in stats],
+                     [amg.amg_get_history(amg.amg_batch_member(hb, k)) for k in range(len(mats))])
+    a, c = out[amg.AMG_LOOP_HOST], out[amg.AMG_LOOP_DEVICE]
+    assert np.array_equal(a[0], c[0]) and a[1] == c[1]
+    assert all(np.array_equal(p, q) for p, q in zip(a[2], c[2]))
+
+
 def test_batch_fp64_against_oracle(env):
     amg, O, torch = env
     mats, rhs = _members(O)

@@ -304,6 +304,39 @@ def test_dataflow_sweeps_repeat_and_transpose(env):
         assert torch.equal(out[0], out[2]), k
 
 
+@pytest.mark.parametrize("name", ["c1-64", "aniso3d-13", "rot2d-100"])
+def test_device_loop_matches_host_loop(env, name):
+    """The FGMRES loop as one CUDA graph with conditional nodes
+    (AMG_LOOP_DEVICE, the default) and the host-driven loop give the same
+    solution, history, counts and status bit for bit: forward and adjoint
+    solves, FP64 and FP32 V-cycles, a converged solve, one stopped by maxit
+    and a repeated solve on the same handle."""
+    amg, O, torch = env
+    p, A, b, Ao, bo = _assemble(env, name)
+    g = torch.as_tensor(np.random.default_rng(4).standard_normal(A.n)).cuda()
+    for prec in (amg.AMG_FP64, amg.AMG_FP32):
+        for maxit in (600, 7):
+            out = {}
+            for loop in (amg.AMG_LOOP_HOST, amg.AMG_LOOP_DEVICE):
+                h = amg.amg_setup(A, vcycle_prec=prec, maxit=maxit, build_adjoint=1, solve_loop=loop)
+                res = []
+                for rep in range(2):
+                    x = torch.zeros_like(b)
+                    st = amg.amg_solve(h, b, x, 1e-8, allow_not_converged=True)
+                    res.append((x.cpu().numpy(), amg.amg_get_history(h), st.iters, st.restarts, st.status,
+                                st.rel_res_true))
+                lam = torch.zeros_like(b)
+                sa = amg.amg_adjoint(h, g, lam, 1e-8, allow_not_converged=True)
+                res.append((lam.cpu().numpy(), amg.amg_get_history(h), sa.iters, sa.restarts, sa.status,
+                            sa.rel_res_true))
+                out[loop] = res
+            for a, c in zip(out[amg.AMG_LOOP_HOST], out[amg.AMG_LOOP_DEVICE]):
+                assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]), (prec, maxit)
+                assert a[2:] == c[2:], (prec, maxit, a[2:], c[2:])
+            if maxit == 7:
+                assert out[amg.AMG_LOOP_DEVICE][0][4] == amg.AMG_ERR_NOT_CONVERGED
+
+
 @pytest.mark.parametrize("name", ["c1-64", "aniso3d-13"])
 def test_cgs2_orthogonalisation(env, name):
     """The classical Gram-Schmidt variant (two passes) reaches the same

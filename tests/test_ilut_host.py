@@ -76,3 +76,23 @@ def test_host_ilut_errors(pkg):
     assert call(rp, bad, v, 0.0, 8) == pkg.AMG_ERR_INVALID_ARG
     nodiag = np.array([0, 1, 0, 0], np.int32)
     assert call(np.array([0, 2, 3], np.int64), nodiag[:3], v[:3], 0.0, 8) == pkg.AMG_ERR_INVALID_ARG
+
+
+def test_table_norm_value_from_library_factors(pkg, oracle_lib):
+    """The paper's comparison of exact and inexact coarse operators
+    (||LU - L~U~|| / ||LU||, Section 3) for the DC1 3D case at 30^3 and
+    tau = 1e-4: the library's host factors give the value that
+    oracle/table_norm.py wrote with the oracle's factors."""
+    import json
+    import os
+    import sys
+    O = oracle_lib
+    here = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
+    sys.path.insert(0, here)
+    import table_norm
+    ref = json.load(open(os.path.join(here, "table_norm.json")))["rows"]["30"]["tau_0.0001"]["rel_error"]
+    Ac = table_norm.coarse_operator(30)
+    rp, ci, v, st = pkg.amg_ilut_host(Ac.row_ptr, Ac.col, Ac.val, 1e-4)
+    assert st == pkg.AMG_OK
+    val = table_norm.factor_error(Ac, O.Csr(Ac.n, rp, ci, v))
+    assert val == ref
