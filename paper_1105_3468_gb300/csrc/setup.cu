@@ -892,91 +892,146 @@ __global__ void k_dense_from_csr(int n, const int *rp, const int *ci, const doub
     }
 }
 
-__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *M, double *f, int *breakdown) {
+// Rows stay where they are: perm[l] is the physical row at logical position
+// l (the position the row would have after the swaps of the sequential
+// algorithm) and pos[r] its inverse.  Step k: the pivot is the first logical
+// row l >= k of largest |m_{perm[l],k}|; perm and pos swap positions k and p;
+// the pivot row R = perm[k] is divided by its diagonal entry; every other
+// row r with f = m_rk != 0 gets m_rj - f m_Rj.  Each value goes through the
+// same operations as in the sequential algorithm, so the inverse is the same
+// bit for bit; logical row l of the inverse is physical row perm[l].
+struct GjPart {
+    double v;      // largest |m_ik| of a row group (-1: none)
+    int l;         // its logical position (first on ties)
+    int pad;
+};
+
+__device__ __forceinline__ bool gj_better(double v, int l, double bv, int bl) {
+    return v > bv || (v == bv && l < bl);
+}
+
+// Pivot of column k: from the row-group partials of the previous elimination
+// (nparts > 0) or by scanning the column (k == 0); swaps positions k and p,
+// stores R and scales the pivot row's columns j > k.
+__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *M, int *perm, int *pos,
+                                                   const GjPart *parts, int nparts, int *R_out, int *breakdown) {
     __shared__ double bv[32];
-    __shared__ int bi[32];
-    __shared__ int piv;
+    __shared__ int bl[32];
+    __shared__ int s_R;
+    __shared__ double s_d;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t w = 2 * (size_t)n;
     double best = -1.0;
     int bidx = n;
-    for (int i = k + tid; i < n; i += blockDim.x) {
-        double a = fabs(M[(size_t)i * 2 * n + k]);
-        if (a > best || (a == best && i < bidx)) { best = a; bidx = i; }
+    if (nparts > 0) {
+        for (int g = tid; g < nparts; g += blockDim.x)
+            if (gj_better(parts[g].v, parts[g].l, best, bidx)) { best = parts[g].v; bidx = parts[g].l; }
+    } else {
+        for (int l = k + tid; l < n; l += blockDim.x) {
+            const double a = fabs(M[(size_t)perm[l] * w + k]);
+            if (gj_better(a, l, best, bidx)) { best = a; bidx = l; }
+        }
     }
     for (int off = 16; off; off >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bidx, off);
-        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+        if (gj_better(ob, oi, best, bidx)) { best = ob; bidx = oi; }
     }
-    if (lane == 0) { bv[warp] = best; bi[warp] = bidx; }
+    if (lane == 0) { bv[warp] = best; bl[warp] = bidx; }
     __syncthreads();
     if (tid == 0) {
         double b = -1.0;
         int p = n;
-        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w)
-            if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
+        for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q)
+            if (gj_better(bv[q], bl[q], b, p)) { b = bv[q]; p = bl[q]; }
         if (!(b > 0.0) || !isfinite(b)) { atomicExch(breakdown, 1); p = k; }
-        piv = p;
+        const int rk = perm[k], rp = perm[p];
+        perm[k] = rp; perm[p] = rk;
+        pos[rp] = k; pos[rk] = p;
+        s_R = rp;
+        *R_out = rp;
+        s_d = M[(size_t)rp * w + k];
     }
     __syncthreads();
-    const int p = piv;
-    double *rk = M + (size_t)k * 2 * n, *rpiv = M + (size_t)p * 2 * n;
-    if (p != k)
-        for (int j = tid; j < 2 * n; j += blockDim.x) { double t = rk[j]; rk[j] = rpiv[j]; rpiv[j] = t; }
-    __syncthreads();
-    const double d = rk[k];
-    __syncthreads();
-    for (int j = tid; j < 2 * n; j += blockDim.x) rk[j] = rk[j] / d;
-    __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : M[(size_t)i * 2 * n + k];
+    double *row = M + (size_t)s_R * w;
+    const double d = s_d;
+    for (size_t j = (size_t)k + tid; j < w; j += blockDim.x) row[j] = __ddiv_rn(row[j], d);
 }
 
-// Rows over blockIdx.y, columns over x: m_ij -= f_i m_kj for i != k, f_i != 0.
-// Only columns j > k that are nonzero in the pivot row are visited.  Columns
-// j <= k of the left half are never read again (later pivots, multipliers and
-// updates use columns beyond their own step, the inverse is the right half),
-// and m_ij - f_i * (+-0) equals m_ij except possibly in the sign of a zero,
-// which no product with the inverse can see (its sums start from +0).  Half
-// the right half is still zero in the pivot row on average, so this halves
-// the traffic without changing any result.
-__global__ void k_gj_elim(int n, int k, double *M, const double *f) {
-    const int w = 2 * n;
-    const double *rk = M + (size_t)k * w;
-    for (int i = blockIdx.y; i < n; i += gridDim.y) {
-        const double fi = f[i];
-        if (i == k || fi == 0.0) continue;
-        double *row = M + (size_t)i * w;
-        for (int j = k + 1 + blockIdx.x * blockDim.x + threadIdx.x; j < w; j += gridDim.x * blockDim.x) {
-            const double r = rk[j];
-            if (r != 0.0) row[j] = __dsub_rn(row[j], __dmul_rn(fi, r));
+// Elimination of column k: physical rows over the row groups (blockIdx.y),
+// columns j > k over x; a thread keeps m_Rj in a register across its rows.
+// Only columns nonzero in the pivot row are updated: m_ij - f (+-0) equals
+// m_ij except possibly in the sign of a zero, which no later product sees.
+// Thread (0, 0) of each row group also records the group's pivot candidate
+// for column k + 1 (largest updated |m_{r,k+1}| over rows with pos[r] > k).
+__global__ void __launch_bounds__(256) k_gj_elim(int n, int k, double *M, const int *pos, const int *R_in,
+                                                 GjPart *parts) {
+    const size_t w = 2 * (size_t)n;
+    const int R = *R_in;
+    const double *rk = M + (size_t)R * w;
+    const int nrows_g = (n + gridDim.y - 1) / gridDim.y;
+    const int r0 = blockIdx.y * nrows_g, r1 = min(n, r0 + nrows_g);
+    const bool cand = k + 1 < n && blockIdx.x == 0 && threadIdx.x == 0;
+    double best = -1.0;
+    int bl = n;
+    for (size_t j = (size_t)k + 1 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < w;
+         j += (size_t)gridDim.x * blockDim.x) {
+        const double r = rk[j];
+        const bool track = cand && j == (size_t)k + 1;
+        if (r == 0.0 && !track) continue;
+        for (int i = r0; i < r1; ++i) {
+            if (i == R) continue;
+            double *row = M + (size_t)i * w;
+            const double fi = row[k];
+            double v = row[j];
+            if (fi != 0.0 && r != 0.0) {
+                v = __dsub_rn(v, __dmul_rn(fi, r));
+                row[j] = v;
+            }
+            if (track) {
+                const int l = pos[i];
+                const double a = fabs(v);
+                if (l > k && gj_better(a, l, best, bl)) { best = a; bl = l; }
+            }
         }
     }
+    if (cand) parts[blockIdx.y] = GjPart{best, bl, 0};
 }
 
-__global__ void k_extract_inverse(int n, const double *M, double *inv) {
+__global__ void k_extract_inverse(int n, const double *M, const int *perm, double *inv) {
     const size_t total = (size_t)n * n;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / n), j = (int)(t % n);
-        inv[t] = M[(size_t)i * 2 * n + n + j];
+        inv[t] = M[(size_t)perm[i] * 2 * n + n + j];
     }
+}
+
+__global__ void k_iota2(int n, int *a, int *b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = b[i] = i;
 }
 
 void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
     const int n = A.n;
-    DBuf<double> M((size_t)n * 2 * n), f(n);
-    DBuf<int> bd(1);
+    DBuf<double> M((size_t)n * 2 * n);
+    DBuf<int> bd(1), perm(n), pos(n), R(1);
+    const int gy = std::max(1, std::min(n, 2 * sm_count()));
+    DBuf<GjPart> parts(gy);
     CU(cudaMemsetAsync(bd.get(), 0, sizeof(int), s));
     k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), M.get());
     CU_LAUNCH("k_dense_from_csr"); count_launch();
+    k_iota2<<<grid_for(n, 256), 256, 0, s>>>(n, perm.get(), pos.get());
+    CU_LAUNCH("k_iota2"); count_launch();
     for (int k = 0; k < n; ++k) {
-        const dim3 eg((2 * n - k - 1 + 255) / 256, n < 65535 ? n : 65535);
-        k_gj_pivot<<<1, 1024, 0, s>>>(n, k, M.get(), f.get(), bd.get());
-        k_gj_elim<<<eg, 256, 0, s>>>(n, k, M.get(), f.get());
+        k_gj_pivot<<<1, 1024, 0, s>>>(n, k, M.get(), perm.get(), pos.get(), parts.get(), k == 0 ? 0 : gy, R.get(),
+                                      bd.get());
+        // columns j > k over x (one thread each per pass), row groups over y
+        const int xb = std::max(1, std::min((2 * n - k - 1 + 255) / 256, 64));
+        k_gj_elim<<<dim3(xb, gy), 256, 0, s>>>(n, k, M.get(), pos.get(), R.get(), parts.get());
         count_launch(2);
     }
     CU_LAUNCH("k_gj_*");
     inv.alloc((size_t)n * n);
-    k_extract_inverse<<<grid_for((size_t)n * n, 256), 256, 0, s>>>(n, M.get(), inv.get());
+    k_extract_inverse<<<grid_for((size_t)n * n, 256), 256, 0, s>>>(n, M.get(), perm.get(), inv.get());
     CU_LAUNCH("k_extract_inverse"); count_launch();
     if (read_int(bd.get(), s)) fail(5, "dense solve of the last level: singular matrix");
 }
