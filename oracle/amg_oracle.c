@@ -11,8 +11,10 @@
  *
  * Compiled with -O2 -ffp-contract=off, so an expression a*b+c rounds twice,
  * as written.  Rounding of multiply-accumulate (the paper does not fix it):
- * the setup (assembly, gradient, ILU(0) factorisation, dense inverse)
- * rounds each product and each sum; the solve phase (matrix-vector
+ * the setup (assembly, gradient, ILU(0) factorisation, the pivot-row
+ * division of the dense inverse) rounds each product and each sum, except
+ * the elimination update of the dense inverse, one fused multiply-add;
+ * the solve phase (matrix-vector
  * products, triangular solves, the dense product, dot products, vector
  * updates, Givens rotations, back substitution) accumulates with fma(),
  * IEEE 754 fused multiply-add with a single rounding.
@@ -777,8 +779,8 @@ void or_ilut_free(or_ilut_t *F)
 /* elimination with partial pivoting on [A | I] (pivot of column k: the  */
 /* first row of largest magnitude at or below k; the pivot row is        */
 /* divided by the pivot, then each other row i with f = m_ik != 0 gets   */
-/* m_ij - f m_kj), applied as a product with the inverse.  a is n x n    */
-/* row-major (input); inv receives A^{-1}.                               */
+/* m_ij - f m_kj as one fused multiply-add), applied as a product with   */
+/* the inverse.  a is n x n row-major (input); inv receives A^{-1}.      */
 /* ------------------------------------------------------------------ */
 static int dense_inverse(int n, const double *a, double *inv)
 {
@@ -805,7 +807,7 @@ static int dense_inverse(int n, const double *a, double *inv)
         for (int i = 0; i < n; ++i) f[i] = (i == k) ? 0.0 : m[(size_t)i * w + k];
         for (int i = 0; i < n; ++i) {
             if (i == k || f[i] == 0.0) continue;
-            for (size_t j = 0; j < w; ++j) m[(size_t)i * w + j] = m[(size_t)i * w + j] - f[i] * m[(size_t)k * w + j];
+            for (size_t j = 0; j < w; ++j) m[(size_t)i * w + j] = fma(-f[i], m[(size_t)k * w + j], m[(size_t)i * w + j]);
         }
     }
     for (int i = 0; i < n; ++i)

@@ -34,7 +34,6 @@ CASES = {
 
 def main(names):
     path = os.path.join(HERE, "workload_iters.json")
-    out = json.load(open(path)) if os.path.exists(path) else {}
     for name in names:
         make, tol, maxit, opts = CASES[name]
         A, b = O.fv_assemble(make())
@@ -43,6 +42,7 @@ def main(names):
         t1 = time.perf_counter()
         _, info = H.fgmres(b, tol=tol, maxit=maxit)
         t2 = time.perf_counter()
+        out = json.load(open(path)) if os.path.exists(path) else {}     # other runs may have written
         out[name] = info.iters
         out[name + "_detail"] = {"status": info.status, "tol": tol, "maxit": maxit, "relres": info.relres,
                                  "setup_s": round(t1 - t0, 2), "solve_s": round(t2 - t1, 2)}

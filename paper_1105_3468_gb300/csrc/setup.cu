@@ -897,73 +897,108 @@ __global__ void k_dense_from_csr(int n, const int *rp, const int *ci, const doub
 // algorithm) and pos[r] its inverse.  Step k: the pivot is the first logical
 // row l >= k of largest |m_{perm[l],k}|; perm and pos swap positions k and p;
 // the pivot row R = perm[k] is divided by its diagonal entry; every other
-// row r with f = m_rk != 0 gets m_rj - f m_Rj.  Each value goes through the
-// same operations as in the sequential algorithm, so the inverse is the same
-// bit for bit; logical row l of the inverse is physical row perm[l].
+// row r with f = m_rk != 0 gets fma(-f, m_Rj, m_rj).  Each value goes through
+// the same operations as in the sequential algorithm, so the inverse is the
+// same bit for bit; logical row l of the inverse is physical row perm[l].
 struct GjPart {
     double v;      // largest |m_ik| of a row group (-1: none)
     int l;         // its logical position (first on ties)
-    int pad;
+    int r;         // its physical row
 };
+
+// x != 0 (either sign of zero counts as zero) as an integer test: FP64
+// compares would use the FP64 pipe, the bound of the elimination on GB300.
+__device__ __forceinline__ bool gj_nonzero(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0;
+}
 
 __device__ __forceinline__ bool gj_better(double v, int l, double bv, int bl) {
     return v > bv || (v == bv && l < bl);
 }
 
-// Pivot of column k: from the row-group partials of the previous elimination
-// (nparts > 0) or by scanning the column (k == 0); swaps positions k and p,
-// stores R and scales the pivot row's columns j > k.
-__global__ void __launch_bounds__(1024) k_gj_pivot(int n, int k, double *M, int *perm, int *pos,
-                                                   const GjPart *parts, int nparts, int *R_out, int *breakdown) {
-    __shared__ double bv[32];
-    __shared__ int bl[32];
-    __shared__ int s_R;
-    __shared__ double s_d;
+// Pivot of column k and the division of the pivot row, over many blocks.
+// Every block reduces the row-group candidates of the previous elimination
+// (nparts > 0) or scans the column (k == 0, nparts == 0) to the same pivot;
+// no block reads perm before block 0 has swapped it (blocks only read perm[k]
+// when the pivot is singular, and then the swap leaves it unchanged); block 0 swaps
+// logical positions k and p and publishes R; each block divides its slice of
+// the pivot row's columns j > k by d = m_Rk (column k itself is never read
+// again, so it keeps the raw d every block reads).
+__global__ void __launch_bounds__(256) k_gj_pivot(int n, int k, double *M, int *perm, int *pos,
+                                                  const GjPart *parts, int nparts, int *R_out, int *breakdown) {
+    __shared__ double bv[8];
+    __shared__ int bl[8], br[8];
+    __shared__ int s_R, s_p;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t w = 2 * (size_t)n;
     double best = -1.0;
-    int bidx = n;
+    int bidx = n, brow = -1;
     if (nparts > 0) {
         for (int g = tid; g < nparts; g += blockDim.x)
-            if (gj_better(parts[g].v, parts[g].l, best, bidx)) { best = parts[g].v; bidx = parts[g].l; }
-    } else {
+            if (gj_better(parts[g].v, parts[g].l, best, bidx)) { best = parts[g].v; bidx = parts[g].l; brow = parts[g].r; }
+    } else {                     // k == 0: perm is still the identity (block 0 swaps it below)
         for (int l = k + tid; l < n; l += blockDim.x) {
-            const double a = fabs(M[(size_t)perm[l] * w + k]);
-            if (gj_better(a, l, best, bidx)) { best = a; bidx = l; }
+            const double a = fabs(M[(size_t)l * w + k]);
+            if (gj_better(a, l, best, bidx)) { best = a; bidx = l; brow = l; }
         }
     }
     for (int off = 16; off; off >>= 1) {
         const double ob = __shfl_down_sync(0xffffffffu, best, off);
         const int oi = __shfl_down_sync(0xffffffffu, bidx, off);
-        if (gj_better(ob, oi, best, bidx)) { best = ob; bidx = oi; }
+        const int orr = __shfl_down_sync(0xffffffffu, brow, off);
+        if (gj_better(ob, oi, best, bidx)) { best = ob; bidx = oi; brow = orr; }
     }
-    if (lane == 0) { bv[warp] = best; bl[warp] = bidx; }
+    if (lane == 0) { bv[warp] = best; bl[warp] = bidx; br[warp] = brow; }
     __syncthreads();
     if (tid == 0) {
         double b = -1.0;
-        int p = n;
+        int p = n, R = -1;
         for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q)
-            if (gj_better(bv[q], bl[q], b, p)) { b = bv[q]; p = bl[q]; }
-        if (!(b > 0.0) || !isfinite(b)) { atomicExch(breakdown, 1); p = k; }
-        const int rk = perm[k], rp = perm[p];
-        perm[k] = rp; perm[p] = rk;
-        pos[rp] = k; pos[rk] = p;
-        s_R = rp;
-        *R_out = rp;
-        s_d = M[(size_t)rp * w + k];
+            if (gj_better(bv[q], bl[q], b, p)) { b = bv[q]; p = bl[q]; R = br[q]; }
+        if (!(b > 0.0) || !isfinite(b)) {              // singular: keep position k (the result is flagged)
+            if (blockIdx.x == 0) atomicExch(breakdown, 1);
+            p = k;
+            R = -1;
+        }
+        s_p = p;
+        s_R = R;
     }
     __syncthreads();
-    double *row = M + (size_t)s_R * w;
-    const double d = s_d;
-    for (size_t j = (size_t)k + tid; j < w; j += blockDim.x) row[j] = __ddiv_rn(row[j], d);
+    int R = s_R;
+    const int p = s_p;
+    if (R < 0) R = perm[k];                           // breakdown: no swap (perm[k] is only written below)
+    if (blockIdx.x == 0 && tid == 0) {
+        const int rk = perm[k];
+        perm[k] = R; perm[p] = rk;
+        pos[R] = k; pos[rk] = p;
+        *R_out = R;
+    }
+    double *row = M + (size_t)R * w;
+    const double d = row[k];
+    constexpr int U = 4;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t j0 = (size_t)k + 1 + blockIdx.x * (size_t)blockDim.x + tid; j0 < w; j0 += U * stride) {
+        double v[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const size_t j = j0 + q * stride;
+            if (j < w) v[q] = row[j];
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const size_t j = j0 + q * stride;
+            if (j < w) row[j] = __ddiv_rn(v[q], d);
+        }
+    }
 }
 
 // Elimination of column k: physical rows over the row groups (blockIdx.y),
 // columns j > k over x; a thread keeps m_Rj in a register across its rows.
-// Only columns nonzero in the pivot row are updated: m_ij - f (+-0) equals
-// m_ij except possibly in the sign of a zero, which no later product sees.
-// Thread (0, 0) of each row group also records the group's pivot candidate
-// for column k + 1 (largest updated |m_{r,k+1}| over rows with pos[r] > k).
+// The update m_ij - f m_Rj is one fused multiply-add.  Only columns nonzero
+// in the pivot row are updated: m_ij - f (+-0) equals m_ij except possibly
+// in the sign of a zero, which no later product sees.  Thread (0, 0) of each
+// row group also records the group's pivot candidate for column k + 1
+// (largest updated |m_{r,k+1}| over rows with pos[r] > k).
 __global__ void __launch_bounds__(256) k_gj_elim(int n, int k, double *M, const int *pos, const int *R_in,
                                                  GjPart *parts) {
     const size_t w = 2 * (size_t)n;
@@ -973,29 +1008,41 @@ __global__ void __launch_bounds__(256) k_gj_elim(int n, int k, double *M, const 
     const int r0 = blockIdx.y * nrows_g, r1 = min(n, r0 + nrows_g);
     const bool cand = k + 1 < n && blockIdx.x == 0 && threadIdx.x == 0;
     double best = -1.0;
-    int bl = n;
+    int bl = n, br = -1;
+    constexpr int U = 8;        // rows whose loads are in flight together
     for (size_t j = (size_t)k + 1 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < w;
          j += (size_t)gridDim.x * blockDim.x) {
         const double r = rk[j];
         const bool track = cand && j == (size_t)k + 1;
-        if (r == 0.0 && !track) continue;
-        for (int i = r0; i < r1; ++i) {
-            if (i == R) continue;
-            double *row = M + (size_t)i * w;
-            const double fi = row[k];
-            double v = row[j];
-            if (fi != 0.0 && r != 0.0) {
-                v = __dsub_rn(v, __dmul_rn(fi, r));
-                row[j] = v;
+        const bool rnz = gj_nonzero(r);
+        if (!rnz && !track) continue;
+        for (int i0 = r0; i0 < r1; i0 += U) {
+            double fv[U], vv[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int i = i0 + q;
+                if (i < r1) {
+                    fv[q] = M[(size_t)i * w + k];
+                    vv[q] = M[(size_t)i * w + j];
+                }
             }
-            if (track) {
-                const int l = pos[i];
-                const double a = fabs(v);
-                if (l > k && gj_better(a, l, best, bl)) { best = a; bl = l; }
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const int i = i0 + q;
+                if (i >= r1 || i == R) continue;
+                if (rnz && gj_nonzero(fv[q])) {
+                    vv[q] = __fma_rn(-fv[q], r, vv[q]);
+                    M[(size_t)i * w + j] = vv[q];
+                }
+                if (track) {
+                    const int l = pos[i];
+                    const double a = fabs(vv[q]);
+                    if (l > k && gj_better(a, l, best, bl)) { best = a; bl = l; br = i; }
+                }
             }
         }
     }
-    if (cand) parts[blockIdx.y] = GjPart{best, bl, 0};
+    if (cand) parts[blockIdx.y] = GjPart{best, bl, br};
 }
 
 __global__ void k_extract_inverse(int n, const double *M, const int *perm, double *inv) {
@@ -1022,8 +1069,9 @@ void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
     k_iota2<<<grid_for(n, 256), 256, 0, s>>>(n, perm.get(), pos.get());
     CU_LAUNCH("k_iota2"); count_launch();
     for (int k = 0; k < n; ++k) {
-        k_gj_pivot<<<1, 1024, 0, s>>>(n, k, M.get(), perm.get(), pos.get(), parts.get(), k == 0 ? 0 : gy, R.get(),
-                                      bd.get());
+        const int pb = std::max(1, std::min((2 * n - k - 1 + 1023) / 1024, sm_count()));
+        k_gj_pivot<<<pb, 256, 0, s>>>(n, k, M.get(), perm.get(), pos.get(), parts.get(), k == 0 ? 0 : gy, R.get(),
+                                      bd.get());      // nparts == 0 only at k == 0
         // columns j > k over x (one thread each per pass), row groups over y
         const int xb = std::max(1, std::min((2 * n - k - 1 + 255) / 256, 64));
         k_gj_elim<<<dim3(xb, gy), 256, 0, s>>>(n, k, M.get(), pos.get(), R.get(), parts.get());

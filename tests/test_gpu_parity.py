@@ -472,9 +472,9 @@ def test_ilut_two_grid_bit_exact(env, name):
     transposed application agrees to rounding (the transposed sweeps sum
     each row in ascending order, the oracle's column-oriented solve of L~^T
     in descending order, as for ILU(0)); the FP64 FGMRES history follows the
-    oracle's within 1e-10 over 20 iterations; on the anisotropic case (the
-    one the mixed-precision test uses) the FP32 V-cycle reaches the true FP64
-    residual 1e-8."""
+    oracle's within 1e-10 over 20 iterations; the FP32 V-cycle reaches the
+    true FP64 residual 1e-8 on both cases (the 64^2 block-kappa case needs
+    about 209 iterations in the FP64 oracle with this reading of ILUT)."""
     amg, O, torch = env
     p, A, b, Ao, bo = _assemble(env, name)
     h = amg.amg_setup(A, coarse_solver=amg.AMG_COARSE_ILUT, ilut_tau=1e-6, build_adjoint=1)
@@ -497,9 +497,9 @@ def test_ilut_two_grid_bit_exact(env, name):
     _, info = H.fgmres(bo, tol=1e-8, maxit=20)
     k = min(len(hist), len(info.hist))
     assert k >= 2 and (np.abs(hist[:k] - info.hist[:k]) / info.hist[:k]).max() <= 1e-10
-    if name == "aniso3d-13":
-        h32 = amg.amg_setup(A, coarse_solver=amg.AMG_COARSE_ILUT, ilut_tau=1e-6, vcycle_prec=amg.AMG_FP32,
-                            maxit=600)
-        x = torch.zeros_like(b)
-        st = amg.amg_solve(h32, b, x, 1e-8)
-        assert st.status == 0 and st.rel_res_true <= 1e-8
+    h32 = amg.amg_setup(A, coarse_solver=amg.AMG_COARSE_ILUT, ilut_tau=1e-6, vcycle_prec=amg.AMG_FP32,
+                        maxit=1000)
+    x = torch.zeros_like(b)
+    st = amg.amg_solve(h32, b, x, 1e-8)
+    print(f"{name}: ILUT two-grid, FP32 V-cycle: {st.iters} iterations")
+    assert st.status == 0 and st.rel_res_true <= 1e-8
