@@ -35,9 +35,13 @@ if ROOT not in sys.path:
 METRIC = "time-to-rel-residual 1e-8 (mixed vs FP64, same GPU); SpMV/cycle HBM GB/s"
 
 
-def workload(name):
-    """(problem, tol, maxit, setup options, description)."""
+def workload(name, size=None):
+    """(problem, tol, maxit, setup options, description).  size: a smaller
+    instance of the 3D recipe (profiling captures only)."""
     from paper_1105_3468_gb300 import workloads as W
+    if name == "c3" and size:
+        return (W.c3_aniso_3d_128(n=size), 1e-8, 3000, {},
+                f"fv3d-{size}^3-aniso-blockkappa (same recipe as the 128^3 workload, for profiling)")
     if name == "c3":
         return (W.c3_aniso_3d_128(), 1e-8, 3000, {},
                 "fv3d-128^3-aniso-blockkappa (2,097,152 unknowns, 14,581,760 nnz, 7-point upwind, 16^3 blocks "
@@ -402,6 +406,8 @@ def main():
     ap.add_argument("--maxit", type=int, default=None, help="override the workload's iteration cap")
     ap.add_argument("--profile-run", action="store_true",
                     help="one setup + solve of the workload (for ncu captures), no timing output")
+    ap.add_argument("--size", type=int, default=None,
+                    help="with --profile-run: a smaller n^3 instance of the 3D recipe (small ncu captures)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--bf16-steps", type=int, default=1, help="steps of the BF16-value V-cycle leg (fp32 runs)")
@@ -444,7 +450,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    prob, tol, maxit, sopts, desc = workload(args.workload)
+    if args.size is not None and not args.profile_run:
+        raise SystemExit("--size is for --profile-run captures only")
+    prob, tol, maxit, sopts, desc = workload(args.workload, args.size)
     if args.maxit is not None:
         maxit = args.maxit
     A, b = amg.assemble_fv(prob)
