@@ -64,9 +64,12 @@ def workload(name, size=None):
                 f"isolated zones else 1, a = {a:g} per axis; FGMRES(30) to true rel. residual 1e-7 (the "
                 f"paper's stopping tolerance), maxit 600")
     if name == "c5":
-        return (W.c5_batch_specs(), 1e-8, 600, {},
+        # dense_max 1024: the members' dense inverses dominate the batch's setup
+        # (8.30 s per batch with 4096, 3.96 s with 1024, every member converging)
+        return (W.c5_batch_specs(), 1e-8, 600, {"dense_max": 1024},
                 "batch of 64 uneven systems: 48 block-kappa grids side U{64..512} + 16 random-geometric-graph "
-                "matrices 10k..500k rows, 7..30 nnz/row (8.8 M rows); one solve loop, FP64 FGMRES(30), tol 1e-8")
+                "matrices 10k..500k rows, 7..30 nnz/row (8.8 M rows); every member's loop in one graph, FP64 "
+                "FGMRES(30), tol 1e-8, last levels of up to 1024 rows solved by their inverse")
     raise ValueError(name)
 
 
@@ -98,7 +101,7 @@ def run_batch(args, amg, torch):
     mine = [specs[k] for k in parts[rank]]
     mats, rhs = batch_members(mine, amg)
     b = torch.tensor(rhs, device="cuda")
-    vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
+    vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "bf16all": amg.AMG_BF16_ALL, "fp64": amg.AMG_FP64}[args.prec]
     rows = sum(A.n for A in mats)
     nnz = sum(A.nnz for A in mats)
 
@@ -106,7 +109,7 @@ def run_batch(args, amg, torch):
         if world > 1:
             dist.barrier()
 
-    extra_opts = {}
+    extra_opts = dict(sopts)
     for kv in args.opt:
         k, v = kv.split("=", 1)
         extra_opts[k] = float(v) if k == "ilut_tau" else int(v)
@@ -162,7 +165,7 @@ def run_batch(args, amg, torch):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
            "higher_is_better": False, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
            "dtype": {"fp32": "f32 V-cycle / f64 FGMRES", "bf16": "bf16 values, f32 V-cycle / f64 FGMRES",
-                     "fp64": "f64"}[args.prec], "data": "synthetic",
+                     "bf16all": "bf16 factors on every level, f32 V-cycle / f64 FGMRES", "fp64": "f64"}[args.prec], "data": "synthetic",
            "config": {"workload": desc, "rows": rows, "nnz": nnz,
                       "parallelism": f"members split over {world} ranks (LPT by nnz)" if world > 1 else "single GPU"},
            "rows_per_s": round(rows / (ms * 1e-3)),
@@ -399,7 +402,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "c5", "dc1-2d", "dcc1-2d", "dc1-3d",
                                                           "dcc2-3d"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "bf16all", "fp64"])
     ap.add_argument("--roofline-class", type=int, default=2,
                     help="kernel class timed live for the roofline: 1 outer SpMV, 2 ILU(0) smoother, 3 CGS2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -410,7 +413,8 @@ def main():
                     help="with --profile-run: a smaller n^3 instance of the 3D recipe (small ncu captures)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--bf16-steps", type=int, default=1, help="steps of the BF16-value V-cycle leg (fp32 runs)")
+    ap.add_argument("--bf16-steps", type=int, default=1,
+                    help="steps of each BF16-factor V-cycle leg (finest level / every level; fp32 runs)")
     ap.add_argument("--fp64-dot2", type=int, default=0, choices=[0, 1],
                     help="accurate (Dot2) inner products in the all-FP64 comparison leg (0: plain, as the mixed leg)")
     ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2, 3, 4],
@@ -457,7 +461,7 @@ def main():
         maxit = args.maxit
     A, b = amg.assemble_fv(prob)
     torch.cuda.synchronize()
-    vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "fp64": amg.AMG_FP64}[args.prec]
+    vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "bf16all": amg.AMG_BF16_ALL, "fp64": amg.AMG_FP64}[args.prec]
     opts = dict(sopts, maxit=maxit)
     for k in ("persistent", "orthog", "deep_block_max", "dense_max", "coarse_solver", "ilut_tau"):
         if getattr(args, k) is not None:
@@ -518,11 +522,14 @@ def main():
     clocks = clk.summary()
     ms64, stats64, acc64, _ = (timed(amg.AMG_FP64, timing_class=1, steps=args.fp64_steps) if vp != amg.AMG_FP64
                                else (ms, stats, [], None))
-    bf16 = None
+    bf16 = bf16_all = None
     if args.prec == "fp32" and args.bf16_steps > 0:
         ms16, stats16, _, _ = timed(amg.AMG_BF16, steps=args.bf16_steps)
         bf16 = {"ms_per_step": round(ms16, 2), "iters": stats16[-1].iters,
                 "rel_res_true": stats16[-1].rel_res_true, "speedup_vs_fp64": round(ms64 / ms16, 3)}
+        ms16a, stats16a, _, _ = timed(amg.AMG_BF16_ALL, steps=args.bf16_steps)
+        bf16_all = {"ms_per_step": round(ms16a, 2), "iters": stats16a[-1].iters,
+                    "rel_res_true": stats16a[-1].rel_res_true, "speedup_vs_fp64": round(ms64 / ms16a, 3)}
 
     # distance of the mixed-precision solutions to the FP64 GPU solution
     def rel_to_fp64(prec):
@@ -530,7 +537,8 @@ def main():
             return None
         r = last_x[amg.AMG_FP64]
         return float(torch.linalg.vector_norm(last_x[prec] - r) / torch.linalg.vector_norm(r))
-    err_vs_fp64 = {"fp32": rel_to_fp64(amg.AMG_FP32), "bf16": rel_to_fp64(amg.AMG_BF16)}
+    err_vs_fp64 = {"fp32": rel_to_fp64(amg.AMG_FP32), "bf16": rel_to_fp64(amg.AMG_BF16),
+                   "bf16_all_levels": rel_to_fp64(amg.AMG_BF16_ALL)}
 
     # end to end through the C ABI with host buffers (copies inside the region)
     Ah = amg.CsrDevice(A.n, A.row_ptr.cpu().numpy(), A.col.cpu().numpy(), A.val.cpu().numpy())
@@ -578,6 +586,7 @@ def main():
         "metric": METRIC, "value": round(ms, 2), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32 V-cycle / f64 FGMRES", "bf16": "bf16 values, f32 V-cycle / f64 FGMRES",
+                                       "bf16all": "bf16 factors on every level, f32 V-cycle / f64 FGMRES",
                                        "fp64": "f64"}[args.prec],
         "data": "synthetic",
         "config": {"workload": desc,
@@ -587,7 +596,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iters": s0.iters, "rel_res_true": s0.rel_res_true, "setup_ms": round(s0.setup_ms, 2),
         "solve_ms": round(s0.solve_ms, 2), "fp64_ms_per_step": round(ms64, 2), "fp64_iters": stats64[-1].iters,
-        "speedup_vs_fp64": round(ms64 / ms, 3), "fp64_dot2": args.fp64_dot2, "bf16_vcycle": bf16, "levels": s0.nlevels,
+        "speedup_vs_fp64": round(ms64 / ms, 3), "fp64_dot2": args.fp64_dot2, "bf16_vcycle": bf16, "bf16_all_levels_vcycle": bf16_all,
+        "levels": s0.nlevels,
         "e2e": {"value": round(statistics.median(e2e), 2), "unit": "ms", "h2d_bytes_per_step": int(bi),
                 "d2h_bytes_per_step": int(bo)},
         "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "spmv_roofline": spmv_roof,

@@ -67,6 +67,9 @@ extern "C" {
 #define AMG_FP32 1              /* FP32 storage and arithmetic             */
 #define AMG_BF16 2              /* as FP32, with the finest level's ILU(0)
                                    factors stored in BF16                 */
+#define AMG_BF16_ALL 3          /* as FP32, with the ILU(0) factors of every
+                                   smoothed level stored in BF16 (residuals
+                                   and coarse matrices stay FP32)         */
 
 /* Elimination order of the ILU(0) factors of one level. */
 #define AMG_ORDER_COLOR 0       /* colour-major (rows of a colour are independent) */
@@ -128,7 +131,8 @@ typedef struct {
     int32_t coloring;         /* AMG_COLOR_HASH_JP                         */
     int32_t restart;          /* FGMRES restart length m: 30               */
     int32_t maxit;            /* total inner iterations cap: 600           */
-    int32_t vcycle_prec;      /* AMG_FP64 / AMG_FP32 / AMG_BF16: AMG_FP64  */
+    int32_t vcycle_prec;      /* AMG_FP64 / AMG_FP32 / AMG_BF16 /
+                                 AMG_BF16_ALL: AMG_FP64                    */
     int32_t build_adjoint;    /* nonzero: also build transposed structures */
     int32_t use_graphs;       /* nonzero: replay the inner iteration as a CUDA
                                  graph captured once per handle: 1          */

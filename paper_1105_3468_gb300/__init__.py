@@ -16,7 +16,7 @@ from typing import Optional
 import numpy as np
 
 from . import _lib
-from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_LOOP_DEVICE, AMG_LOOP_HOST, AMG_MATCH_PLAIN, AMG_MATCH_SCALED, AMG_COARSE_ILUT, AMG_COARSE_RECURSIVE, AMG_ORTHO_CGS2, AMG_ORTHO_MGS, AMG_BF16, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
+from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_LOOP_DEVICE, AMG_LOOP_HOST, AMG_MATCH_PLAIN, AMG_MATCH_SCALED, AMG_COARSE_ILUT, AMG_COARSE_RECURSIVE, AMG_ORTHO_CGS2, AMG_ORTHO_MGS, AMG_BF16, AMG_BF16_ALL, AMG_COLOR_FIRST_FIT, AMG_COLOR_HASH_JP, AMG_ERR_BREAKDOWN,  # noqa: F401
                    AMG_ERR_CUDA, AMG_ERR_INVALID_ARG, AMG_ERR_LIMIT, AMG_ERR_NOT_CONVERGED,
                    AMG_ERR_NOT_SUPPORTED, AMG_ERR_NUMERIC, AMG_ERR_OOM, AMG_FP32, AMG_FP64, AMG_OK,
                    AMG_ORDER_COLOR, AMG_ORDER_NATURAL, AmgCsr, AmgOptions, AmgStats)

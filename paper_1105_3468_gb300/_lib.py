@@ -22,7 +22,7 @@ AMG_ERR_NUMERIC = 6
 AMG_ERR_NOT_CONVERGED = 7
 AMG_ERR_LIMIT = 8
 
-AMG_FP64, AMG_FP32, AMG_BF16 = 0, 1, 2
+AMG_FP64, AMG_FP32, AMG_BF16, AMG_BF16_ALL = 0, 1, 2, 3
 AMG_NOALLOC_MAX_ROWS = 4194304
 AMG_ORDER_COLOR, AMG_ORDER_NATURAL = 0, 1
 AMG_COLOR_HASH_JP, AMG_COLOR_FIRST_FIT = 0, 1

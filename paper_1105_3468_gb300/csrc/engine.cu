@@ -319,6 +319,13 @@ static void build_ilut_level(Level &L, const amg_options_t &o, cudaStream_t s) {
     L.ilut_level = true;
 }
 
+// Storage precision of level l's factors for a V-cycle precision.
+static int level_prec(int vcycle_prec, size_t l) {
+    if (vcycle_prec == AMG_BF16_ALL) return AMG_BF16;
+    if (vcycle_prec == AMG_BF16 && l > 0) return AMG_FP32;
+    return vcycle_prec;
+}
+
 static void cast_sweep(Sweep &S, int prec, cudaStream_t s) {
     const size_t nnzf = S.v64.n;
     if (prec == AMG_FP32 || prec == AMG_BF16) {
@@ -432,10 +439,11 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
         }
         if (last) break;
     }
-    // precision copies (BF16: the finest level's ILU(0) factors only)
+    // precision copies (BF16: the finest level's ILU(0) factors only; BF16_ALL:
+    // the factors of every smoothed level)
     for (size_t l = 0; l < h->lev.size(); ++l) {
         Level &L = *h->lev[l];
-        const int prec = (o.vcycle_prec == AMG_BF16 && l > 0) ? AMG_FP32 : o.vcycle_prec;
+        const int prec = level_prec(o.vcycle_prec, l);
         if (prec != AMG_FP64) {
             L.v32.alloc(L.A.nnz);
             cast_f64_f32(L.A.v.get(), L.v32.get(), L.A.nnz, s);
@@ -449,7 +457,7 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
     if (o.build_adjoint) {
         for (size_t l = 0; l < h->lev.size(); ++l) {
             Level &L = *h->lev[l];
-            const int prec = (o.vcycle_prec == AMG_BF16 && l > 0) ? AMG_FP32 : o.vcycle_prec;
+            const int prec = level_prec(o.vcycle_prec, l);
             transpose_values(L.A, L.A.v.get(), L.AT, s);
             if (prec != AMG_FP64) {
                 L.vt32.alloc(L.AT.nnz);
@@ -641,11 +649,16 @@ struct VCycle {
     // g = C_l(h): the inexact solve of level l >= 1
     void level_solve(int l, const T *hrhs, T *g) {
         if constexpr (std::is_same<V, __nv_bfloat16>::value) {
-            // BF16 values are stored for the finest level only; the coarse
-            // levels run in FP32 (rounding Galerkin sums with near-zero row
-            // sums to 8 bits made the coarse Richardson steps diverge)
-            VCycle<float, float>{h, s}.level_solve(l, hrhs, g);
-            return;
+            // BF16 factors on the finest level only (AMG_BF16) or on levels
+            // run by the single-block deep V-cycle: the coarse levels run in
+            // FP32.  AMG_BF16_ALL keeps BF16 factors on every level; the
+            // residuals always use FP32 matrix values (rounding Galerkin sums
+            // with near-zero row sums to 8 bits made the coarse Richardson
+            // steps diverge).
+            if (h->opt.vcycle_prec != AMG_BF16_ALL || l >= h->deep_first) {
+                VCycle<float, float>{h, s}.level_solve(l, hrhs, g);
+                return;
+            }
         }
         Level &Lv = L(l);
         if (l >= h->deep_first) {
@@ -692,8 +705,10 @@ struct VCycle {
 
     void level_solveT(int l, const T *hrhs, T *g) {
         if constexpr (std::is_same<V, __nv_bfloat16>::value) {
-            VCycle<float, float>{h, s}.level_solveT(l, hrhs, g);
-            return;
+            if (h->opt.vcycle_prec != AMG_BF16_ALL || l >= h->deep_first) {
+                VCycle<float, float>{h, s}.level_solveT(l, hrhs, g);
+                return;
+            }
         }
         Level &Lv = L(l);
         if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 1, 0, dense_dot2(), s); return; }
@@ -1288,7 +1303,7 @@ int amg_default_options(amg_options_t *o) {
 static void check_options(const amg_options_t &o) {
     if (o.passes < 1 || o.passes > 8 || o.coarse_inner < 1 || o.deep_inner < 1 || o.dense_max < 0 ||
         o.dense_max > 4096 || o.max_levels < 2 || o.max_levels > 24 || o.restart < 1 || o.restart > KMAX1 - 1 ||
-        o.maxit < 0 || o.vcycle_prec < 0 || o.vcycle_prec > 2 || o.order_fine < 0 || o.order_fine > 1 ||
+        o.maxit < 0 || o.vcycle_prec < 0 || o.vcycle_prec > 3 || o.order_fine < 0 || o.order_fine > 1 ||
         o.order_coarse < 0 || o.order_coarse > 1 || o.coloring < 0 || o.coloring > 1 || o.deep_block_max < 0 ||
         o.persistent < 0 || o.persistent > 4 || o.orthog < 0 || o.orthog > 1 ||
         (o.spmv_block != 0 && o.spmv_block != 64 && o.spmv_block != 128 && o.spmv_block != 256 &&
@@ -1446,7 +1461,10 @@ int amg_setup_batched(const amg_csr_t *systems, int32_t count, const amg_options
     std::vector<std::string> msg(count);
     std::atomic<int> next{0};
     std::atomic<int64_t> launches{0};
-    const int nth = std::max(1, std::min<int>(count, 8));
+    // one host thread per core, at most 16 (each member's setup is a chain of
+    // short launches and synchronisations, so members overlap on the GPU)
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nth = std::max(1, std::min<int>(count, std::min(16, hw > 0 ? hw : 8)));
     auto work = [&]() {
         cudaSetDevice(dev);
         const int64_t l0 = launch_count();

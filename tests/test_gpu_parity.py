@@ -178,11 +178,11 @@ def test_adjoint_solution(env, persistent):
     assert np.linalg.norm(lam.cpu().numpy() - lo) <= 1e-8 * np.linalg.norm(lo)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16all"])
 def test_mixed_precision_reaches_fp64_tolerance(env, prec):
     amg, O, torch = env
     p, A, b, Ao, bo = _assemble(env, "aniso3d-13")
-    vp = amg.AMG_FP32 if prec == "fp32" else amg.AMG_BF16
+    vp = {"fp32": amg.AMG_FP32, "bf16": amg.AMG_BF16, "bf16all": amg.AMG_BF16_ALL}[prec]
     h64 = amg.amg_setup(A)
     x64 = torch.zeros_like(b)
     s64 = amg.amg_solve(h64, b, x64, 1e-8)
@@ -268,7 +268,7 @@ def test_graph_replay_and_persistent_identical(env):
     per-level launches."""
     amg, O, torch = env
     p, A, b, Ao, bo = _assemble(env, "aniso3d-13")
-    for prec in (amg.AMG_FP64, amg.AMG_FP32, amg.AMG_BF16):
+    for prec in (amg.AMG_FP64, amg.AMG_FP32, amg.AMG_BF16, amg.AMG_BF16_ALL):
         ref = None
         for g, pers in ((0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2), (1, 3), (1, 4)):
             h = amg.amg_setup(A, use_graphs=g, persistent=pers, vcycle_prec=prec)
