@@ -52,6 +52,7 @@ struct Level {
     // dense last level
     bool dense = false;
     DBuf<double> inv;
+    DBuf<float> inv32;                    // FP32 copy for the FP32 / BF16 V-cycles
     // SELL-32 copies for the outer FP64 SpMV (level 0 only)
     Sell sell, sellT;
     // workspace (vector type of the V-cycle, allocated as bytes)
@@ -451,6 +452,10 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
         if (!L.dense) {
             cast_sweep(L.fwd, prec, s);
             cast_sweep(L.bwd, prec, s);
+        } else if (prec != AMG_FP64) {
+            const size_t nn = (size_t)L.A.n * L.A.n;
+            L.inv32.alloc(nn);
+            cast_f64_f32(L.inv.get(), L.inv32.get(), nn, s);
         }
     }
     // adjoint structures
@@ -582,6 +587,15 @@ struct VCycle {
     // when the Arnoldi inner products are Dot2 too (the dot2 option)
     bool dense_dot2() const { return std::is_same<T, double>::value && use_dot2(h); }
 
+    // g = A_L^{-1} h (transpose: A_L^{-T} h) on the dense last level: the FP64
+    // inverse in the FP64 V-cycle, its FP32 copy in the FP32 / BF16 ones
+    void dense_apply(Level &Lv, const T *hrhs, T *g, int transpose) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (Lv.inv32.n) { dense_solve_f32(Lv.A.n, Lv.inv32.get(), hrhs, g, transpose, s); return; }
+        }
+        dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, transpose, 0, dense_dot2(), s);
+    }
+
     // t = S^{-1} in (transpose: S^{-T} in); y is scratch for the first solve
     void smooth(Level &Lv, const T *in, T *y, T *t, bool transpose) {
         Sweep &F = transpose ? Lv.fwdT : Lv.fwd;
@@ -667,7 +681,7 @@ struct VCycle {
             deep_vcycle<T, V>(d, nlev() - l, s);
             return;
         }
-        if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 0, 0, dense_dot2(), s); return; }
+        if (Lv.dense) { dense_apply(Lv, hrhs, g, 0); return; }
         if (Lv.ilut_level) { smooth(Lv, hrhs, ws(Lv.wy), g, false); return; }   // g = (L~ U~)^{-1} h
         const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
         T *res = ws(Lv.wres);
@@ -711,7 +725,7 @@ struct VCycle {
             }
         }
         Level &Lv = L(l);
-        if (Lv.dense) { dense_solve<T>(Lv.A.n, Lv.inv.get(), hrhs, g, 1, 0, dense_dot2(), s); return; }
+        if (Lv.dense) { dense_apply(Lv, hrhs, g, 1); return; }
         if (Lv.ilut_level) { smooth(Lv, hrhs, ws(Lv.wy), g, true); return; }    // g = (L~ U~)^{-T} h
         const int k = l == 1 ? h->opt.coarse_inner : h->opt.deep_inner;
         T *res = ws(Lv.wres);
@@ -1461,10 +1475,10 @@ int amg_setup_batched(const amg_csr_t *systems, int32_t count, const amg_options
     std::vector<std::string> msg(count);
     std::atomic<int> next{0};
     std::atomic<int64_t> launches{0};
-    // one host thread per core, at most 16 (each member's setup is a chain of
-    // short launches and synchronisations, so members overlap on the GPU)
-    const int hw = (int)std::thread::hardware_concurrency();
-    const int nth = std::max(1, std::min<int>(count, std::min(16, hw > 0 ? hw : 8)));
+    // 8 host threads: each member's setup is a chain of short launches and
+    // synchronisations, so members overlap on the GPU (16 threads measured
+    // slower on the batch workload: setup 3.72 s against 3.47 s)
+    const int nth = std::max(1, std::min<int>(count, 8));
     auto work = [&]() {
         cudaSetDevice(dev);
         const int64_t l0 = launch_count();

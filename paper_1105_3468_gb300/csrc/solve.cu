@@ -1119,6 +1119,33 @@ void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int 
                                                                                              mode);
     CU_LAUNCH("k_dense_gemv"); count_launch();
 }
+// FP32 inverse, FP32 accumulation: lane r sums the terms j = r, r + 32, ...
+// with fused multiply-adds, the 32 partial sums are added by halving.
+__global__ void __launch_bounds__(32 * DENSE_WARPS) k_dense_gemv_f32(int n, const float *__restrict__ inv,
+                                                                     const float *__restrict__ h,
+                                                                     float *__restrict__ g, int transpose) {
+    extern __shared__ float dense_hf[];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) dense_hf[j] = h[j];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * DENSE_WARPS + (threadIdx.x >> 5); i < n; i += gridDim.x * DENSE_WARPS) {
+        float acc = 0.f;
+        if (transpose) {
+            for (int j = lane; j < n; j += 32) acc = __fmaf_rn(inv[(size_t)j * n + i], dense_hf[j], acc);
+        } else {
+            const float *row = inv + (size_t)i * n;
+            for (int j = lane; j < n; j += 32) acc = __fmaf_rn(row[j], dense_hf[j], acc);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) acc = __fadd_rn(acc, __shfl_down_sync(0xffffffffu, acc, off));
+        if (lane == 0) g[i] = acc;
+    }
+}
+void dense_solve_f32(int n, const float *inv, const float *h, float *g, int transpose, cudaStream_t s) {
+    const int blocks = (n + DENSE_WARPS - 1) / DENSE_WARPS;
+    k_dense_gemv_f32<<<blocks, 32 * DENSE_WARPS, sizeof(float) * (size_t)n, s>>>(n, inv, h, g, transpose);
+    CU_LAUNCH("k_dense_gemv_f32"); count_launch();
+}
 template void dense_solve<double>(int, const double *, const double *, double *, int, int, bool, cudaStream_t);
 template void dense_solve<float>(int, const double *, const float *, float *, int, int, bool, cudaStream_t);
 

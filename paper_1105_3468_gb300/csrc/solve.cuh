@@ -88,6 +88,9 @@ void convert_f32_f64(size_t n, const float *in, double *out, cudaStream_t s);
 // dot2: each row as an inner product as if in twice the working precision
 template <typename T>
 void dense_solve(int n, const double *inv, const T *h, T *g, int transpose, int mode, bool dot2, cudaStream_t s);
+// The same from an FP32 copy of the inverse, accumulated in FP32 (the FP32 /
+// BF16 V-cycles).
+void dense_solve_f32(int n, const float *inv, const float *h, float *g, int transpose, cudaStream_t s);
 
 // K = st->j + 1 basis vectors (read on the device)
 // Smoothers with more schedule levels than this (forward + backward) run as
