@@ -149,7 +149,8 @@ def run_batch(args, amg, torch):
             ms = float(t.item())
         res[prec] = (ms, st, amg.amg_launch_counter() - l0)
     ms, st, launches = res[vp]
-    summary = ([(s.iters, s.status) for s in st], rows, nnz, launches)
+    setup_each = sorted(((round(s.setup_ms, 1), A.n) for s, A in zip(st, mats)), reverse=True)
+    summary = ([(s.iters, s.status) for s in st], rows, nnz, launches, setup_each)
     if world > 1:
         got = [None] * world
         dist.all_gather_object(got, summary)
@@ -172,6 +173,8 @@ def run_batch(args, amg, torch):
            "iters_min_max": [min(i for i, _ in per_member), max(i for i, _ in per_member)],
            "all_converged": all(s == 0 for _, s in per_member), "gpu_launches": int(launches),
            "setup_solve_ms_last_step": [[round(a, 1), round(c, 1)] for p, a, c in split if p == vp][-1],
+           "member_setup_ms": {"sum": round(sum(t for g in got for t, _ in g[4]), 1),
+                               "largest_5_ms_rows": sorted((x for g in got for x in g[4]), reverse=True)[:5]},
            "options": extra_opts}
     if amg.AMG_FP64 in res and vp != amg.AMG_FP64:
         out["fp64_ms_per_step"] = round(res[amg.AMG_FP64][0], 2)

@@ -268,8 +268,10 @@ int amg_ilut_host(int32_t n, const int64_t *row_ptr, const int32_t *col, const d
  * Krylov iteration), stopping when the true relative residual
  * ||b - A x|| / ||b|| <= tol (Section 3 stopping rule).  b: host or device
  * [n]; x: host or device [n], read as the initial guess, written with the
- * result.  stats may be NULL.  Returns AMG_ERR_NOT_CONVERGED when maxit is
- * reached (x holds the last iterate), AMG_ERR_NUMERIC for NaN/Inf. */
+ * result.  stats may be NULL.  The loop runs on the device (solve_loop) unless
+ * a kernel class is timed.  Returns AMG_ERR_NOT_CONVERGED when maxit is
+ * reached (x holds the last iterate), AMG_ERR_NUMERIC for NaN/Inf,
+ * AMG_ERR_LIMIT when a bounded device wait gave up. */
 int amg_solve(amg_handle_t *h, const double *b, double *x, double tol, amg_stats_t *stats);
 
 /* Solves the adjoint system A^T lambda = g by FGMRES preconditioned with
@@ -281,8 +283,9 @@ int amg_adjoint(amg_handle_t *h, const double *g, double *lambda, double tol, am
 
 /* ------------------------------------------------------------- batches */
 /* Sets up `count` independent systems (the batched path): one hierarchy per
- * system, built concurrently from a few host threads, each system on its own
- * internal stream.  The per-system results are those amg_setup gives for
+ * system, built concurrently from 8 host threads, each system on its own
+ * internal stream (setup memory comes from the library's stream-ordered pool,
+ * so the setups do not synchronise one another).  The per-system results are those amg_setup gives for
  * that system alone.  systems: host array of `count` CSR descriptors (their
  * arrays host or device).  Errors as amg_setup, the message naming the
  * first failing system; nothing is kept on error. */
@@ -290,13 +293,17 @@ int amg_setup_batched(const amg_csr_t *systems, int32_t count, const amg_options
                       amg_handle_t **out);
 /* Solves every system of a batched handle: b_cat and x_cat (host or device)
  * hold the systems' vectors back to back, at the offsets amg_batch_size
- * reports.  One host loop advances all systems: each active system queues
- * one FGMRES inner iteration (a CUDA graph replay on its stream, so the
- * systems run concurrently), then each is collected; a system that has
- * converged or failed drops out.  per_system (host, may be NULL) receives
- * `count` stats.  Returns the first error, else AMG_ERR_NOT_CONVERGED if any
- * system hit maxit, else AMG_OK.  Each system's iterates are exactly those
- * of amg_solve on that system alone. */
+ * reports.  With solve_loop = AMG_LOOP_DEVICE (default) every system's
+ * FGMRES loop is one root chain of a single CUDA graph (conditional nodes;
+ * each system's done flag lives in device memory), so the whole batch is one
+ * graph launch and one synchronisation, built on the first call and replayed
+ * afterwards.  With AMG_LOOP_HOST one host loop advances all systems: each
+ * active system queues one inner iteration (a graph replay on its stream),
+ * then each is collected; a converged or failed system drops out.
+ * per_system (host, may be NULL) receives `count` stats.  Returns the first
+ * error, else AMG_ERR_NOT_CONVERGED if any system hit maxit, else AMG_OK.
+ * Each system's iterates are exactly those of amg_solve on that system
+ * alone, with either loop. */
 int amg_solve_batched(amg_handle_t *h, const double *b_cat, double *x_cat, double tol,
                       amg_stats_t *per_system);
 /* Number of systems and their row offsets (host, count + 1 entries; may be

@@ -1341,7 +1341,10 @@ int amg_setup(const amg_csr_t *A, const amg_options_t *opt, void *stream, amg_ha
     CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&h->entry_ev, cudaEventDisableTiming));
     enter(h.get());
-    setup_impl(h.get(), A);
+    {
+        AllocScope scope(h->stream);       // setup buffers: stream-ordered pool on the handle's stream
+        setup_impl(h.get(), A);
+    }
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h.release();
     return AMG_OK;
@@ -1381,6 +1384,7 @@ int amg_update_values(amg_handle_t *h, const double *val) {
     CU_LAUNCH("k_rp32_to_64"); count_launch();
     amg_csr_t A{n, (int64_t)L0.A.nnz, rp64.get(), L0.A.ci.get(), val};
     try {
+        AllocScope scope(nh->stream);
         setup_impl(nh.get(), &A, &frozen);
         CU(cudaStreamSynchronize(nh->stream));
     } catch (...) {

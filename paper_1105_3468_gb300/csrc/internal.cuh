@@ -38,29 +38,46 @@ int64_t launch_count();
 
 // ------------------------------------------------------------------ memory
 // Device allocation with an OOM status instead of an exception type.
-void *dmalloc(size_t bytes);
-void dfree(void *p);
+// Inside an AllocScope (a setup on one stream), allocations come from the
+// library's stream-ordered memory pool on the scope's stream and frees are
+// stream-ordered on it: no device-wide synchronisation, so setups of many
+// systems on their own streams (a batch) overlap.  Outside a scope, plain
+// cudaMalloc / cudaFree.  A pooled buffer freed outside a scope is freed by
+// cudaFree, which does not wait: its owner synchronises first (handles do
+// before they release their buffers).
+void *dmalloc(size_t bytes, bool *pooled);
+void dfree(void *p, bool pooled);
+struct AllocScope {
+    cudaStream_t prev;
+    explicit AllocScope(cudaStream_t s);
+    ~AllocScope();
+};
 
 template <typename T>
 struct DBuf {
     T *p = nullptr;
     size_t n = 0;
+    bool pooled = false;
     DBuf() = default;
     explicit DBuf(size_t count) { alloc(count); }
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
-    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), pooled(o.pooled) { o.p = nullptr; o.n = 0; o.pooled = false; }
     DBuf &operator=(DBuf &&o) noexcept {
-        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; pooled = o.pooled;
+            o.p = nullptr; o.n = 0; o.pooled = false;
+        }
         return *this;
     }
     ~DBuf() { release(); }
     void alloc(size_t count) {
         release();
         n = count;
-        p = count ? static_cast<T *>(dmalloc(count * sizeof(T))) : nullptr;
+        p = count ? static_cast<T *>(dmalloc(count * sizeof(T), &pooled)) : nullptr;
     }
-    void release() { if (p) dfree(p); p = nullptr; n = 0; }
+    void release() { if (p) dfree(p, pooled); p = nullptr; n = 0; pooled = false; }
     T *get() const { return p; }
     size_t bytes() const { return n * sizeof(T); }
 };

@@ -6,6 +6,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 namespace amg {
 
@@ -25,19 +26,67 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
     fail(2, buf);
 }
 
-void *dmalloc(size_t bytes) {
+// The stream of the enclosing AllocScope on this thread (nullptr: none).
+static thread_local cudaStream_t t_alloc_stream = nullptr;
+static thread_local bool t_alloc_scoped = false;
+
+AllocScope::AllocScope(cudaStream_t s) : prev(t_alloc_stream) {
+    t_alloc_stream = s;
+    t_alloc_scoped = true;
+}
+AllocScope::~AllocScope() {
+    t_alloc_stream = prev;
+    t_alloc_scoped = prev != nullptr;
+}
+
+// One pool per device, created on first use.  Up to 1 GiB of freed memory
+// stays in the pool between synchronisations; memory freed on one stream is
+// reused by another only when its free has already completed (no
+// dependencies inserted between the streams).
+static cudaMemPool_t pool_for_current_device() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(4, "memory pool: device ordinal >= 64");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        CU(cudaMemPoolCreate(&pools[dev], &props));
+        uint64_t keep = 1ull << 30;
+        CU(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+        int off = 0;
+        CU(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolReuseAllowInternalDependencies, &off));
+    }
+    return pools[dev];
+}
+
+void *dmalloc(size_t bytes, bool *pooled) {
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e;
+    if (t_alloc_scoped && t_alloc_stream) {
+        e = cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), t_alloc_stream);
+        *pooled = true;
+    } else {
+        e = cudaMalloc(&p, bytes);
+        *pooled = false;
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         char buf[160];
-        snprintf(buf, sizeof buf, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        snprintf(buf, sizeof buf, "device allocation (%zu bytes): %s", bytes, cudaGetErrorString(e));
         fail(e == cudaErrorMemoryAllocation ? 3 : 2, buf);
     }
     return p;
 }
 
-void dfree(void *p) { cudaFree(p); }
+void dfree(void *p, bool pooled) {
+    if (pooled && t_alloc_scoped && t_alloc_stream) cudaFreeAsync(p, t_alloc_stream);
+    else cudaFree(p);
+}
 
 int sm_count() {
     static const int sms = [] {               // initialised once, thread-safe

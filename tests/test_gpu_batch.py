@@ -6,7 +6,8 @@
   solutions within 1e-8;
 * converged systems drop out while the others continue (uneven iteration
   counts), and per-system statuses are reported.
-Members follow the batch recipe at small sizes: block-kappa grids (8x8
+Members follow the batch recipe at small sizes (and, in the last test, the full
+64-member batch workload): block-kappa grids (8x8
 blocks, a = (1, 0.5)) and random-geometric-graph matrices, b ~ N(0,1).
 """
 import numpy as np
@@ -125,3 +126,53 @@ def test_batch_reports_per_system_failure(env):
     assert all(s.status == amg.AMG_ERR_NOT_CONVERGED and s.iters == 3 for s in stats)
     with pytest.raises(amg.AmgError):
         amg.amg_solve(hb, b, x, 1e-8)               # a batch handle needs amg_solve_batched
+
+
+def test_fullsize_batch_sampled_members(env):
+    """The 64-member batch workload (48 block-kappa grids of side 64..512 and
+    16 random-geometric-graph matrices of 10k..500k rows) in the configuration
+    the benchmark times (last levels of up to 1024 rows solved exactly, every
+    member's loop in one graph): all members converge with the FP64 and the
+    FP32 V-cycle; for four sampled members (the smallest and a mid-size grid,
+    the smallest and the largest graph matrix) the FP64 history agrees with
+    the oracle's within 1e-10 over 20 iterations and the FP64 solution within
+    1e-8; the FP32 V-cycle's solutions are printed and bounded (1e-6)."""
+    amg, O, torch = env
+    specs = W.c5_batch_specs()
+    mats, hmats, rhs = [], [], []
+    for sp in specs:
+        if sp.kind == "grid":
+            A, _ = O.fv_assemble(W.batch_grid_problem(sp))
+        else:
+            A = O.as_csr(W.rgg_matrix(sp.size, sp.nnz_per_row, sp.seed))
+        hmats.append(A)
+        mats.append(amg.CsrDevice.from_host(A))
+        rhs.append(W.batch_rhs(sp, A.n))
+    b = torch.tensor(np.concatenate(rhs), device="cuda")
+    out = {}
+    for prec in (amg.AMG_FP64, amg.AMG_FP32):
+        hb = amg.amg_setup_batched(mats, vcycle_prec=prec, dense_max=1024)
+        _, offs = amg.amg_batch_size(hb)
+        x = torch.zeros_like(b)
+        stats = amg.amg_solve_batched(hb, b, x, 1e-8)
+        assert all(s.status == 0 and s.rel_res_true <= 1e-8 for s in stats)
+        out[prec] = (hb, offs, x.cpu().numpy(), stats)
+    grids = [k for k, s in enumerate(specs) if s.kind == "grid"]
+    rggs = [k for k, s in enumerate(specs) if s.kind == "rgg"]
+    by_n = lambda ks: sorted(ks, key=lambda k: hmats[k].n)
+    sample = [by_n(grids)[0], by_n(grids)[len(grids) // 2], by_n(rggs)[0], by_n(rggs)[-1]]
+    hb, offs, x64, _ = out[amg.AMG_FP64]
+    _, _, x32, st32 = out[amg.AMG_FP32]
+    for k in sample:
+        A = hmats[k]
+        H = O.Hierarchy(A, dense_max=1024)
+        xo, info = H.fgmres(rhs[k], tol=1e-8)
+        assert info.status == 0
+        hist = amg.amg_get_history(amg.amg_batch_member(hb, k))
+        m = min(21, len(hist), len(info.hist))
+        hdiff = float((np.abs(hist[:m] - info.hist[:m]) / info.hist[:m]).max())
+        e64 = float(np.linalg.norm(x64[offs[k]:offs[k + 1]] - xo) / np.linalg.norm(xo))
+        e32 = float(np.linalg.norm(x32[offs[k]:offs[k + 1]] - xo) / np.linalg.norm(xo))
+        print(f"batch member {k} ({specs[k].kind}, {A.n} rows): oracle {info.iters} iterations, FP32 "
+              f"{st32[k].iters}; history diff {hdiff:.1e}, |x - x_oracle|/|x_oracle| FP64 {e64:.1e}, FP32 {e32:.1e}")
+        assert hdiff <= 1e-10 and e64 <= 1e-8 and e32 <= 1e-6
