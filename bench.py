@@ -420,10 +420,10 @@ def main():
                     help="steps of each BF16-factor V-cycle leg (finest level / every level; fp32 runs)")
     ap.add_argument("--fp64-dot2", type=int, default=0, choices=[0, 1],
                     help="accurate (Dot2) inner products in the all-FP64 comparison leg (0: plain, as the mixed leg)")
-    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--persistent", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="ILU(0) sweep schedule: 0 per-level launches, 1 level barriers, 2 dataflow, "
                          "3 dataflow on the finest level only, 4 dataflow where the level does not fit "
-                         "the shared-memory cluster kernel")
+                         "the shared-memory cluster kernel, 5 as 3 with a grid-stencil finest level in tiles")
     ap.add_argument("--orthog", type=int, default=None, choices=[0, 1], help="0 modified, 1 classical (2-pass) Gram-Schmidt")
     ap.add_argument("--dense-max", type=int, default=None,
                     help="largest level (rows) solved exactly by its dense inverse")

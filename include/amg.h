@@ -149,10 +149,18 @@ typedef struct {
                                  (no level barriers; bounded waits).  3:
                                  dataflow on the finest level only, as 1
                                  elsewhere.  4: dataflow on every level too
-                                 large for the shared-memory kernel.  All
-                                 five give bit-identical results.  A wait
-                                 that gives up returns AMG_ERR_LIMIT.
-                                 Default: 3                                 */
+                                 large for the shared-memory kernel.  5:
+                                 as 3, but a finest level in natural order
+                                 whose matrix is a 5-point (2D) or 7-point
+                                 (3D) grid stencil (detected from the
+                                 pattern) is solved in grid tiles: one
+                                 block per 16^3 (64^2) tile with the tile's
+                                 wavefronts in shared memory, only the
+                                 faces between tiles through global memory
+                                 (amg_get_tile_grid reports the tiling).
+                                 All six give bit-identical results.  A
+                                 wait that gives up returns AMG_ERR_LIMIT.
+                                 Default: 5                                 */
     int32_t deep_block_max;   /* levels >= 2 with at most this many rows (and
                                  all levels below them) run their V-cycle in
                                  one thread block when deep_inner == 1;
@@ -356,6 +364,12 @@ int amg_spmv_noalloc(const amg_csr_t *A, const double *x, double *y, void *strea
  * the next level (-1 if last), [6] colours (0 in natural order),
  * [7] sweep levels of the backward solve.  info: host [8]. */
 int amg_get_level_info(amg_handle_t *h, int32_t level, int64_t *info);
+/* Grid tiling of the finest level's smoother (persistent = 5): info[0] 1 when
+ * the finest level is solved in grid tiles, else 0 (and the rest 0);
+ * [1..3] the detected grid nx, ny, nz (nz = 1 in 2D); [4..6] the tile
+ * extents; [7] the number of tiles.  info: host [8].  AMG_ERR_INVALID_ARG
+ * for a null argument or a batched handle. */
+int amg_get_tile_grid(amg_handle_t *h, int64_t *info);
 int amg_num_levels(amg_handle_t *h, int32_t *nlevels);
 
 /* Launch geometry the outer SpMV of h uses (picked by the autotuner unless

@@ -24,6 +24,7 @@ from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_LOOP_DEVICE, AMG_LOOP_HOST, AMG_MAT
 __all__ = [
     "AmgError", "Handle", "amg_default_options", "amg_setup", "amg_destroy", "amg_solve",
     "amg_adjoint", "amg_get_history", "amg_precond_apply", "amg_spmv", "amg_get_level_info",
+    "amg_get_tile_grid",
     "amg_num_levels", "amg_get_aggregates", "amg_get_matrix", "amg_get_pass_matrix",
     "amg_get_colors", "amg_get_ilu", "amg_fv_assemble", "amg_fv_grad_logk", "amg_fv_assemble_logk",
     "amg_fv_grad_logk_iso", "amg_version",
@@ -312,6 +313,14 @@ def amg_get_level_info(h: Handle, level: int) -> dict:
     _check(lib().amg_get_level_info(h.ptr, level, info.ctypes.data), "amg_get_level_info")
     keys = ["n", "nnz", "fwd_levels", "dense", "n_pass1", "n_next", "ncol", "bwd_levels"]
     return {k: int(v) for k, v in zip(keys, info)}
+
+
+def amg_get_tile_grid(h: Handle) -> dict:
+    """The finest level's grid tiling (persistent = 5): tiled, grid, tile extents, tile count."""
+    info = np.zeros(8, np.int64)
+    _check(lib().amg_get_tile_grid(h.ptr, info.ctypes.data), "amg_get_tile_grid")
+    return {"tiled": bool(info[0]), "grid": tuple(int(v) for v in info[1:4]),
+            "tile": tuple(int(v) for v in info[4:7]), "ntiles": int(info[7])}
 
 
 def amg_get_aggregates(h: Handle, level: int, pass_: int = 0) -> np.ndarray:

@@ -58,6 +58,8 @@ struct Level {
     // workspace (vector type of the V-cycle, allocated as bytes)
     DBuf<char> wt, wy, wr, wres, wh, wg, wf;
     int wy_sent = 0;                      // element size of the sentinel wy holds (dataflow sweeps), 0: none
+    // the smoother in grid tiles (finest level, natural-order stencil, persistent 5)
+    std::unique_ptr<TilePlan> tiles;
 };
 
 }  // namespace amg
@@ -402,6 +404,8 @@ static void tune_sell(Sell &SL, const amg_options_t &o, cudaStream_t s) {
 
 // frozen (amg_update_values): the previous hierarchy's per-level, per-pass
 // maps; levels keep the same shape, only the numbers are recomputed.
+static void build_tiles(amg_handle *h, cudaStream_t s);
+
 static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
                        std::vector<std::vector<PassData>> *frozen = nullptr) {
     const amg_options_t &o = h->opt;
@@ -476,6 +480,7 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
         }
         h->adjoint_ready = true;
     }
+    build_tiles(h, s);
     // SELL-32 copies of A (and A^T) for the outer FP64 products
     build_sell(h->lev[0]->A, h->lev[0]->A.v.get(), h->lev[0]->sell, s);
     if (o.build_adjoint) build_sell(h->lev[0]->AT, h->lev[0]->AT.v.get(), h->lev[0]->sellT, s);
@@ -601,10 +606,17 @@ struct VCycle {
         Sweep &F = transpose ? Lv.fwdT : Lv.fwd;
         Sweep &B = transpose ? Lv.bwdT : Lv.bwd;
         const int fd = transpose ? 1 : 0, bd = transpose ? 0 : 1;
-        // algorithmic bytes: factor values + columns + schedule rows/pointers,
-        // the diagonal, in read once, y written and read, out written
+        // persistent 5: as 3, the finest level in grid tiles when its matrix
+        // is a natural-order grid stencil (tiles.cu)
+        const TilePlan *P = Lv.tiles.get();
+        const bool tiled = h->opt.persistent == 5 && P && P->tsz == sizeof(T) && P->vsz == sizeof(V) &&
+                           (transpose ? P->fwdT.c.n : P->fwd.c.n);
+        // algorithmic bytes: factor values (+ columns and schedule
+        // rows/pointers, which the tiled solve does not read), the diagonal,
+        // in read once, y written and read, out written
         const double n = Lv.A.n;
-        const double bytes = (sizeof(V) + 4.0) * (double)(F.v64.n + B.v64.n) + 12.0 * 2.0 * n +
+        const double bytes = (sizeof(V) + (tiled ? 0.0 : 4.0)) * (double)(F.v64.n + B.v64.n) +
+                             (tiled ? 0.0 : 12.0 * 2.0 * n) +
                              sizeof(T) * (1.0 + (B.d64.n || F.d64.n ? 1.0 : 0.0) + 3.0) * n;
         tmark_begin(h, 2);
         // persistent 2: dataflow solve (no level barriers) on every level
@@ -613,9 +625,14 @@ struct VCycle {
         // persistent 1: one cooperative launch with level barriers where there
         // are many schedule levels (natural order), colour classes as
         // separate launches; persistent 0: one launch per schedule level
-        const bool dataflow = h->opt.persistent == 2 || (h->opt.persistent == 3 && &Lv == h->lev[0].get()) ||
+        const bool finest = &Lv == h->lev[0].get();
+        const bool dataflow = h->opt.persistent == 2 ||
+                              ((h->opt.persistent == 3 || h->opt.persistent == 5) && finest) ||
                               (h->opt.persistent == 4 && !sweep_fits_dsm(Lv.A.n, F.nlev, B.nlev, sizeof(T)));
-        if (dataflow) {
+        if (tiled) {
+            sweep_pair_tiles<T, V>(*P, transpose ? P->fwdT : P->fwd, transpose ? P->bwdT : P->bwd, in, y, t,
+                                   h->bar.get(), h->err.get(), s);
+        } else if (dataflow) {
             if (Lv.wy_sent != (int)sizeof(T)) {
                 fill_sentinel<T>(y, (size_t)Lv.A.n, s);
                 Lv.wy_sent = (int)sizeof(T);
@@ -762,6 +779,34 @@ template <> SweepView<float, float> VCycle<float, float>::view(Sweep &S) {
 template <> SweepView<float, __nv_bfloat16> VCycle<float, __nv_bfloat16>::view(Sweep &S) {
     return SweepView<float, __nv_bfloat16>{S.nlev, S.lev_ptr.data(), S.dlev.get(), S.rows.get(), S.rp.get(),
                                            S.ci.get(), S.v16.get(), S.d32.n ? S.d32.get() : nullptr};
+}
+
+// The finest level's smoother in tile layout (persistent 5): built when the
+// level is in natural order and its matrix a 2D / 3D grid stencil; without
+// a plan the level keeps the dataflow solve.
+template <typename T, typename V>
+static void build_tiles_t(amg_handle *h, Level &L, cudaStream_t s) {
+    std::unique_ptr<TilePlan> P(new TilePlan());
+    if (!tile_plan_build(L.A, *P, sizeof(T), sizeof(V), s)) return;
+    tile_prepare<T, V>(*P);
+    VCycle<T, V> vc{h, s};
+    if (!tile_factor_build<T, V>(*P, vc.view(L.fwd), false, P->fwd, s)) return;
+    if (!tile_factor_build<T, V>(*P, vc.view(L.bwd), true, P->bwd, s)) return;
+    if (h->opt.build_adjoint) {
+        if (!tile_factor_build<T, V>(*P, vc.view(L.fwdT), false, P->fwdT, s)) return;
+        if (!tile_factor_build<T, V>(*P, vc.view(L.bwdT), true, P->bwdT, s)) return;
+    }
+    L.tiles = std::move(P);
+}
+static void build_tiles(amg_handle *h, cudaStream_t s) {
+    Level &L = *h->lev[0];
+    L.tiles.reset();
+    if (h->opt.persistent != 5 || L.dense || L.ilut_level || L.order != AMG_ORDER_NATURAL) return;
+    switch (level_prec(h->opt.vcycle_prec, 0)) {
+    case AMG_FP64: build_tiles_t<double, double>(h, L, s); break;
+    case AMG_FP32: build_tiles_t<float, float>(h, L, s); break;
+    default: build_tiles_t<float, __nv_bfloat16>(h, L, s); break;
+    }
 }
 
 // Device descriptors of the levels run by the single-block V-cycle.
@@ -1057,8 +1102,17 @@ static int run_end(Run &R, amg_stats_t *stats) {
         CU(cudaMemsetAsync(h->err.get(), 0, sizeof(int), s));
         CU(cudaMemsetAsync(h->bar.get(), 0, 2 * sizeof(unsigned int), s));
         CU(cudaStreamSynchronize(s));
-        for (auto &L : h->lev) L->wy_sent = 0;
-        t_last_error = "a grid-barrier or dataflow wait gave up (results invalid)";
+        // a wait that gave up leaves values in place of sentinels: restore
+        // them here (a captured graph does not refill them)
+        for (auto &L : h->lev) {
+            if (L->wy_sent == (int)sizeof(double))
+                fill_sentinel<double>(reinterpret_cast<double *>(L->wy.get()), L->A.n, s);
+            else if (L->wy_sent == (int)sizeof(float))
+                fill_sentinel<float>(reinterpret_cast<float *>(L->wy.get()), L->A.n, s);
+            if (L->tiles) tile_mailbox_reset(*L->tiles, s);
+        }
+        CU(cudaStreamSynchronize(s));
+        t_last_error = "a grid-barrier, dataflow or tile wait gave up (results invalid)";
         R.status = AMG_ERR_LIMIT;
     }
     const auto t1 = std::chrono::steady_clock::now();
@@ -1300,7 +1354,7 @@ int amg_default_options(amg_options_t *o) {
     o->vcycle_prec = AMG_FP64;
     o->build_adjoint = 0;
     o->use_graphs = 1;
-    o->persistent = 3;
+    o->persistent = 5;
     o->deep_block_max = 0;
     o->orthog = AMG_ORTHO_MGS;
     o->spmv_block = 0;
@@ -1319,7 +1373,7 @@ static void check_options(const amg_options_t &o) {
         o.dense_max > 4096 || o.max_levels < 2 || o.max_levels > 24 || o.restart < 1 || o.restart > KMAX1 - 1 ||
         o.maxit < 0 || o.vcycle_prec < 0 || o.vcycle_prec > 3 || o.order_fine < 0 || o.order_fine > 1 ||
         o.order_coarse < 0 || o.order_coarse > 1 || o.coloring < 0 || o.coloring > 1 || o.deep_block_max < 0 ||
-        o.persistent < 0 || o.persistent > 4 || o.orthog < 0 || o.orthog > 1 ||
+        o.persistent < 0 || o.persistent > 5 || o.orthog < 0 || o.orthog > 1 ||
         (o.spmv_block != 0 && o.spmv_block != 64 && o.spmv_block != 128 && o.spmv_block != 256 &&
          o.spmv_block != 512) ||
         (o.spmv_unroll != 0 && o.spmv_unroll != 2 && o.spmv_unroll != 4 && o.spmv_unroll != 8) || o.dot2 < -1 ||
@@ -1680,6 +1734,23 @@ int amg_get_level_info(amg_handle_t *h, int32_t level, int64_t *info) {
     info[5] = L.n_next;
     info[6] = L.ncol;
     info[7] = L.dense ? 0 : L.bwd.nlev;
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_get_tile_grid(amg_handle_t *h, int64_t *info) {
+    ABI_TRY
+    if (!h || !info) fail(AMG_ERR_INVALID_ARG, "null argument");
+    if (!h->subs.empty()) fail(AMG_ERR_INVALID_ARG, "amg_get_tile_grid: batched handle");
+    const TilePlan *P = h->lev[0]->tiles.get();
+    for (int q = 0; q < 8; ++q) info[q] = 0;
+    if (P) {
+        const TileGeom &g = P->g;
+        info[0] = 1;
+        info[1] = g.nx; info[2] = g.ny; info[3] = g.nz;
+        info[4] = g.tx; info[5] = g.ty; info[6] = g.tz;
+        info[7] = g.ntiles;
+    }
     return AMG_OK;
     ABI_CATCH
 }

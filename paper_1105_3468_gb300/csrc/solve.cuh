@@ -74,6 +74,50 @@ template <typename T, typename V>
 void sweep_pair_df(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in, T *y,
                    T *out, unsigned int *bar, int *err, cudaStream_t s);
 template <typename T> void fill_sentinel(T *x, size_t n, cudaStream_t s);
+// Grid-tiled triangular solves of a natural-order 5-point (2D) or 7-point
+// (3D) stencil level (tiles.cu).  Tiles of tx x ty x tz rows (powers of two);
+// step coordinates of a row are its local coordinates in its tile, reversed
+// for the backward solve.
+struct TileGeom {
+    int dim, nx, ny, nz;          // grid (nz = 1 in 2D)
+    int tx, ty, tz, lx, ly;       // tile extents, log2 tx, log2 ty
+    int ntx, nty, ntz, ntiles;    // tiles per axis, total
+    int tv, nd, fs, ne, nq;       // rows per tile, steps per tile, mailbox face stride, halo entries, axes
+};
+// One triangular solve's factor values in tile layout: c [ntiles][nq][tv]
+// (slot q: the q-th neighbour the row consumes), d [ntiles][tv] the diagonal
+// (empty when the solve has none); position within a tile = local index
+// (i + tx (j + ty k)) in step coordinates.
+struct TileFactor {
+    DBuf<char> c, d;
+};
+struct TilePlan {
+    TileGeom g{};
+    size_t tsz = 0, vsz = 0;      // vector and factor value sizes the plan is built for
+    DBuf<int> hwoff;              // [nd + 1] first halo entry of each step
+    DBuf<unsigned int> hent;      // [ne] halo entries: face | step << 2 | a << 12 | b << 22
+    DBuf<int> torder;             // [ntiles] tiles by anti-diagonal
+    DBuf<char> mb[2];             // mailboxes [ntiles][3][fs] of the forward and backward phases
+    TileFactor fwd, bwd, fwdT, bwdT;
+    int blocks = 0;               // cooperative grid of the tile kernel (tile_prepare)
+};
+// Detects the grid of a natural-order stencil matrix and builds the plan's
+// geometry, tables and mailboxes; false (plan untouched) when the matrix's
+// lower offsets do not describe a 2D / 3D grid.  The factor build verifies
+// every row against the stencil.
+bool tile_plan_build(const DCsr &A, TilePlan &P, size_t tsz, size_t vsz, cudaStream_t s);
+void tile_mailbox_reset(TilePlan &P, cudaStream_t s);
+// S in tile layout (mirror: the backward solve); false when a row's stored
+// entries are not its stencil neighbours in ascending column order.
+template <typename T, typename V>
+bool tile_factor_build(const TilePlan &P, const SweepView<T, V> &S, bool mirror, TileFactor &F, cudaStream_t s);
+// Kernel attributes and the co-resident grid for this plan's layout.
+template <typename T, typename V> void tile_prepare(TilePlan &P);
+// y = F^{-1} in, out = B^{-1} y: one cooperative launch, a grid barrier
+// between the two solves; err set when a bounded wait gave up.
+template <typename T, typename V>
+void sweep_pair_tiles(const TilePlan &P, const TileFactor &F, const TileFactor &B, const T *in, T *y, T *out,
+                      unsigned int *bar, int *err, cudaStream_t s);
 // True when a level's two solve vectors (elem bytes per row each) and its
 // level pointers fit the shared-memory sweep kernel.
 bool sweep_fits_dsm(int n, int nlev_f, int nlev_b, size_t elem);

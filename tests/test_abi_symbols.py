@@ -64,7 +64,7 @@ def test_setup_rejects_bad_options_before_any_device_call(lib):
     A = _lib.AmgCsr()
     out = C.c_void_p()
     for field, value in (("coarse_solver", 2), ("ilut_tau", -1.0), ("ilut_tau", float("nan")),
-                         ("ilut_tau", float("inf")), ("dense_max", 4097), ("persistent", 5), ("passes", 0),
+                         ("ilut_tau", float("inf")), ("dense_max", 4097), ("persistent", 6), ("passes", 0),
                          ("match_weight", 2), ("match_weight", -1), ("solve_loop", 2),
                          ("vcycle_prec", 4)):
         o = pkg.amg_default_options()
