@@ -238,11 +238,19 @@ class ClockSampler:
 SMOOTHER_PROFILE = os.path.join(ROOT, "profiles", "smoother_dram_fv3d128_one_iteration.md")
 
 
+def sweep_sources_sha256():
+    """SHA-256 of the sweep kernels' sources (solve.cu, tiles.cu, devsync.cuh, in that order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("solve.cu", "tiles.cu", "devsync.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1105_3468_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def profiled_traffic(workload_name):
     """DRAM bytes per smoother application from the committed ncu summary,
     or None when the summary is for another workload or the sweep kernels'
     source changed since it was captured."""
-    import hashlib
     if workload_name != "c3":
         return None
     try:
@@ -254,9 +262,7 @@ def profiled_traffic(workload_name):
         if ":" in ln and ln.strip().startswith("- `"):
             k, v = ln.strip()[3:].split("`", 1)
             vals[k] = v.split(":", 1)[1].strip().strip("`")
-    src = os.path.join(ROOT, "paper_1105_3468_gb300", "csrc", "solve.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if vals.get("solve_cu_sha256") != sha:
+    if vals.get("sweep_sources_sha256") != sweep_sources_sha256():
         return None
     try:
         return int(vals["dram_bytes_per_application"])
@@ -566,7 +572,7 @@ def main():
     if tot_n:
         achieved = tot_b / tot_n / (tot_ms / tot_n * 1e-3) / 1e9
         names = {1: "outer FP64 SpMV w = A z_j",
-                 2: "ILU(0) smoother applications, all levels (k_sweep_df / k_sweep_pair / k_sweep_pair_dsm)",
+                 2: "ILU(0) smoother applications, all levels (k_sweep_tiles / k_sweep_pair / k_sweep_pair_dsm)",
                  3: "CGS2 pass"}
         roof = {"bound": "hbm", "kernel": names.get(args.roofline_class), "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": "measured" if peaks else "fallback", "unit": "GB/s",

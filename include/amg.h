@@ -370,6 +370,14 @@ int amg_get_level_info(amg_handle_t *h, int32_t level, int64_t *info);
  * extents; [7] the number of tiles.  info: host [8].  AMG_ERR_INVALID_ARG
  * for a null argument or a batched handle. */
 int amg_get_tile_grid(amg_handle_t *h, int64_t *info);
+/* The smoother variant of level l's last application, kind[0] for S^{-1}
+ * and kind[1] for S^{-T} (-1: not applied yet): 0 one launch per schedule
+ * level, 1 one block, 2 a grid of up to 8 blocks run as one cluster, 3
+ * cooperative grid with grid barriers, 4 one cluster with both solve
+ * vectors replicated in every CTA's shared memory, 5 dataflow solve, 6 grid
+ * tiles.  kind: host [2].  Which variant runs depends on the persistent
+ * option and the level's size; all give the same bits. */
+int amg_get_sweep_kind(amg_handle_t *h, int32_t level, int32_t *kind);
 int amg_num_levels(amg_handle_t *h, int32_t *nlevels);
 
 /* Launch geometry the outer SpMV of h uses (picked by the autotuner unless

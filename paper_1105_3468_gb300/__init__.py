@@ -24,7 +24,7 @@ from ._lib import (AMG_NOALLOC_MAX_ROWS, AMG_LOOP_DEVICE, AMG_LOOP_HOST, AMG_MAT
 __all__ = [
     "AmgError", "Handle", "amg_default_options", "amg_setup", "amg_destroy", "amg_solve",
     "amg_adjoint", "amg_get_history", "amg_precond_apply", "amg_spmv", "amg_get_level_info",
-    "amg_get_tile_grid",
+    "amg_get_tile_grid", "amg_get_sweep_kind",
     "amg_num_levels", "amg_get_aggregates", "amg_get_matrix", "amg_get_pass_matrix",
     "amg_get_colors", "amg_get_ilu", "amg_fv_assemble", "amg_fv_grad_logk", "amg_fv_assemble_logk",
     "amg_fv_grad_logk_iso", "amg_version",
@@ -321,6 +321,16 @@ def amg_get_tile_grid(h: Handle) -> dict:
     _check(lib().amg_get_tile_grid(h.ptr, info.ctypes.data), "amg_get_tile_grid")
     return {"tiled": bool(info[0]), "grid": tuple(int(v) for v in info[1:4]),
             "tile": tuple(int(v) for v in info[4:7]), "ntiles": int(info[7])}
+
+
+SWEEP_KINDS = ("levels", "block", "cluster_grid", "grid", "dsm_replicated", "dataflow", "tiles")
+
+
+def amg_get_sweep_kind(h: Handle, level: int) -> tuple:
+    """The smoother variant of the level's last application (forward, transposed); None if not applied."""
+    k = np.zeros(2, np.int32)
+    _check(lib().amg_get_sweep_kind(h.ptr, level, k.ctypes.data), "amg_get_sweep_kind")
+    return tuple(SWEEP_KINDS[v] if v >= 0 else None for v in k)
 
 
 def amg_get_aggregates(h: Handle, level: int, pass_: int = 0) -> np.ndarray:

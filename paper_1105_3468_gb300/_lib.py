@@ -86,6 +86,7 @@ SIGNATURES = {
     "amg_spmv_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, _P, _P]),
     "amg_get_level_info": (C.c_int, [_P, C.c_int32, _P]),
     "amg_get_tile_grid": (C.c_int, [_P, _P]),
+    "amg_get_sweep_kind": (C.c_int, [_P, C.c_int32, _P]),
     "amg_num_levels": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "amg_get_spmv_config": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "amg_get_aggregates": (C.c_int, [_P, C.c_int32, C.c_int32, _P]),

@@ -60,6 +60,7 @@ struct Level {
     int wy_sent = 0;                      // element size of the sentinel wy holds (dataflow sweeps), 0: none
     // the smoother in grid tiles (finest level, natural-order stencil, persistent 5)
     std::unique_ptr<TilePlan> tiles;
+    int sweep_kind[2] = {-1, -1};         // smoother variant of the last application (SWEEP_KIND_*), forward / transposed
 };
 
 }  // namespace amg
@@ -629,21 +630,26 @@ struct VCycle {
         const bool dataflow = h->opt.persistent == 2 ||
                               ((h->opt.persistent == 3 || h->opt.persistent == 5) && finest) ||
                               (h->opt.persistent == 4 && !sweep_fits_dsm(Lv.A.n, F.nlev, B.nlev, sizeof(T)));
+        int kind;
         if (tiled) {
             sweep_pair_tiles<T, V>(*P, transpose ? P->fwdT : P->fwd, transpose ? P->bwdT : P->bwd, in, y, t,
                                    h->bar.get(), h->err.get(), s);
+            kind = SWEEP_KIND_TILES;
         } else if (dataflow) {
             if (Lv.wy_sent != (int)sizeof(T)) {
                 fill_sentinel<T>(y, (size_t)Lv.A.n, s);
                 Lv.wy_sent = (int)sizeof(T);
             }
             sweep_pair_df<T, V>(view(F), fd, view(B), bd, in, y, t, h->bar.get(), h->err.get(), s);
+            kind = SWEEP_KIND_DATAFLOW;
         } else if (h->opt.persistent && F.nlev + B.nlev > PERSISTENT_MIN_LEVELS) {
-            sweep_pair_coop<T, V>(view(F), fd, view(B), bd, in, y, t, h->bar.get(), h->err.get(), s);
+            kind = sweep_pair_coop<T, V>(view(F), fd, view(B), bd, in, y, t, h->bar.get(), h->err.get(), s);
         } else {
             sweep<T, V>(view(F), in, y, fd, s);
             sweep<T, V>(view(B), y, t, bd, s);
+            kind = SWEEP_KIND_LEVELS;
         }
+        Lv.sweep_kind[transpose ? 1 : 0] = kind;
         tmark_end(h, 2, bytes);
     }
     bool has_child(int l) { return l + 1 < nlev() && L(l).n_next > 0; }
@@ -1751,6 +1757,16 @@ int amg_get_tile_grid(amg_handle_t *h, int64_t *info) {
         info[4] = g.tx; info[5] = g.ty; info[6] = g.tz;
         info[7] = g.ntiles;
     }
+    return AMG_OK;
+    ABI_CATCH
+}
+
+int amg_get_sweep_kind(amg_handle_t *h, int32_t level, int32_t *kind) {
+    ABI_TRY
+    if (!kind) fail(AMG_ERR_INVALID_ARG, "null kind");
+    Level &L = level_of(h, level);
+    kind[0] = L.sweep_kind[0];
+    kind[1] = L.sweep_kind[1];
     return AMG_OK;
     ABI_CATCH
 }

@@ -301,7 +301,10 @@ __device__ __forceinline__ void level_wait(unsigned int *bar, int *err, const Le
 // plus barrier) to arrive; only the values of earlier rows remain on the
 // critical path.  Positions beyond the first a thread owns in a level (levels
 // wider than the grid) are read directly.
-constexpr int SWEEP_PF = 8;
+#ifndef AMG_SWEEP_PF
+#define AMG_SWEEP_PF 12
+#endif
+constexpr int SWEEP_PF = AMG_SWEEP_PF;
 constexpr int SWEEP_CLUSTER_MAX = 8;   // portable cluster size
 constexpr size_t SWEEP_DL_MAX_BYTES = 48 * 1024;   // level pointers staged in shared memory
 
@@ -310,10 +313,10 @@ struct RowA {
     int t, i, k0, k1;
     T d;
 };
-template <typename T, typename V>
+template <typename T, typename V, int PF = SWEEP_PF>
 struct RowB {
-    int c[SWEEP_PF];
-    V v[SWEEP_PF];
+    int c[PF];
+    V v[PF];
     T in;
 };
 
@@ -333,13 +336,13 @@ __device__ __forceinline__ RowA<T> row_a(const SweepView<T, V> &S, const int *dl
 
 // IN: 0 global input (plain load), 1 global input written earlier in this
 // launch (read past L1), 2 shared-memory input.
-template <int IN, typename T, typename V>
-__device__ __forceinline__ RowB<T, V> row_b(const SweepView<T, V> &S, const RowA<T> &a, const T *in) {
-    RowB<T, V> b;
+template <int IN, typename T, typename V, int PF = SWEEP_PF>
+__device__ __forceinline__ RowB<T, V, PF> row_b(const SweepView<T, V> &S, const RowA<T> &a, const T *in) {
+    RowB<T, V, PF> b;
     b.in = T(0);
     if (a.t < 0) return b;
 #pragma unroll
-    for (int q = 0; q < SWEEP_PF; ++q)
+    for (int q = 0; q < PF; ++q)
         if (a.k0 + q < a.k1) { b.c[q] = S.ci[a.k0 + q]; b.v[q] = S.v[a.k0 + q]; }
     b.in = IN == 1 ? __ldcg(in + a.i) : in[a.i];
     return b;
@@ -347,18 +350,18 @@ __device__ __forceinline__ RowB<T, V> row_b(const SweepView<T, V> &S, const RowA
 
 // out_i = (in_i - sum_k v_k x_{c_k}) [/ d] for a pipelined row; x read past L1
 // (COHERENT) or directly (shared memory).
-template <bool COHERENT, typename T, typename V>
-__device__ __forceinline__ T row_value(const SweepView<T, V> &S, const RowA<T> &a, const RowB<T, V> &b, const T *x,
+template <bool COHERENT, typename T, typename V, int PF = SWEEP_PF>
+__device__ __forceinline__ T row_value(const SweepView<T, V> &S, const RowA<T> &a, const RowB<T, V, PF> &b, const T *x,
                                        int with_diag) {
-    T xv[SWEEP_PF];
+    T xv[PF];
 #pragma unroll
-    for (int q = 0; q < SWEEP_PF; ++q)
+    for (int q = 0; q < PF; ++q)
         if (a.k0 + q < a.k1) xv[q] = COHERENT ? __ldcg(x + b.c[q]) : x[b.c[q]];
     T acc = b.in;
 #pragma unroll
-    for (int q = 0; q < SWEEP_PF; ++q)
+    for (int q = 0; q < PF; ++q)
         if (a.k0 + q < a.k1) acc = msub(acc, val_as<T, V>(b.v[q]), xv[q]);
-    acc = row_sub<COHERENT, T, V>(acc, a.k0 + SWEEP_PF, a.k1, S.ci, S.v, x);
+    acc = row_sub<COHERENT, T, V>(acc, a.k0 + PF, a.k1, S.ci, S.v, x);
     return with_diag ? acc / a.d : acc;
 }
 
@@ -419,6 +422,12 @@ __global__ void __launch_bounds__(256) k_sweep_pair(SweepView<T, V> F, int f_dia
 // threads per block: 512 for FP32 vectors, 256 for FP64 (register budget)
 template <typename T> __host__ __device__ constexpr int dsm_threads() { return sizeof(T) == 8 ? 256 : 512; }
 constexpr int DSM_MAX_CTAS = 8;
+// row entries prefetched a level ahead in the cluster kernel (deeper spills
+// registers at 512 threads)
+#ifndef AMG_DSM_PF
+#define AMG_DSM_PF 8
+#endif
+constexpr int DSM_PF = AMG_DSM_PF;
 constexpr size_t DSM_MAX_BYTES = 200 * 1024;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -465,12 +474,12 @@ __device__ __forceinline__ void dsm_phase(const SweepView<T, V> &S, const int *d
         }
     };
     RowA<T> a0 = row_a(S, dl, 0, tid, with_diag), a1 = row_a(S, dl, 1, tid, with_diag);
-    RowB<T, V> b0 = row_b<IN>(S, a0, in);
+    RowB<T, V, DSM_PF> b0 = row_b<IN, T, V, DSM_PF>(S, a0, in);
     for (int l = 0; l < S.nlev; ++l) {
-        const RowB<T, V> b1 = row_b<IN>(S, a1, in);
+        const RowB<T, V, DSM_PF> b1 = row_b<IN, T, V, DSM_PF>(S, a1, in);
         const RowA<T> a2 = row_a(S, dl, l + 2, tid, with_diag);
         if (a0.t >= 0) {
-            finish(a0.i, row_value<false, T, V>(S, a0, b0, xs, with_diag));
+            finish(a0.i, row_value<false, T, V, DSM_PF>(S, a0, b0, xs, with_diag));
             const int e = dl[l + 1];
             for (int t = a0.t + nthr; t < e; t += nthr) {      // levels wider than the grid
                 const int i = S.rows[t];
@@ -585,7 +594,7 @@ static bool sweep_pair_dsm(const SweepView<T, V> &F, int f_diag, const SweepView
 }
 
 template <typename T, typename V>
-void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
+int sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
                      T *y, T *out, unsigned int *bar, int *err, cudaStream_t s) {
     static const int grid = [] {               // initialised once, thread-safe
         int per_sm = 0;
@@ -595,7 +604,7 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
     int maxw = 0;
     for (int l = 0; l < F.nlev; ++l) maxw = max(maxw, F.lev_ptr[l + 1] - F.lev_ptr[l]);
     for (int l = 0; l < B.nlev; ++l) maxw = max(maxw, B.lev_ptr[l + 1] - B.lev_ptr[l]);
-    if (sweep_pair_dsm<T, V>(F, f_diag, B, b_diag, in, out, maxw, s)) return;
+    if (sweep_pair_dsm<T, V>(F, f_diag, B, b_diag, in, out, maxw, s)) return SWEEP_KIND_DSM_REPLICATED;
     int g = (maxw + 255) / 256;
     if (g > grid) g = grid;
     if (g < 1) g = 1;
@@ -604,7 +613,7 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
     if (dl_bytes > SWEEP_DL_MAX_BYTES) {          // too many schedule levels to stage: one launch per level
         sweep<T, V>(F, in, y, f_diag, s);
         sweep<T, V>(B, y, out, b_diag, s);
-        return;
+        return SWEEP_KIND_LEVELS;
     }
     if (g == 1) {
         k_sweep_pair<T, V, 2><<<1, 256, dl_bytes, s>>>(f, f_diag, b, b_diag, in, y, out, bar, err);
@@ -630,12 +639,13 @@ void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V>
         CU(cudaLaunchCooperativeKernel((const void *)k_sweep_pair<T, V, 0>, dim3(g), dim3(256), args, dl_bytes, s));
     }
     count_launch();
+    return g == 1 ? SWEEP_KIND_BLOCK : g <= SWEEP_CLUSTER_MAX ? SWEEP_KIND_CLUSTER_GRID : SWEEP_KIND_GRID;
 }
-template void sweep_pair_coop<double, double>(const SweepView<double, double> &, int, const SweepView<double, double> &,
+template int sweep_pair_coop<double, double>(const SweepView<double, double> &, int, const SweepView<double, double> &,
                                               int, const double *, double *, double *, unsigned int *, int *, cudaStream_t);
-template void sweep_pair_coop<float, float>(const SweepView<float, float> &, int, const SweepView<float, float> &, int,
+template int sweep_pair_coop<float, float>(const SweepView<float, float> &, int, const SweepView<float, float> &, int,
                                             const float *, float *, float *, unsigned int *, int *, cudaStream_t);
-template void sweep_pair_coop<float, __nv_bfloat16>(const SweepView<float, __nv_bfloat16> &, int,
+template int sweep_pair_coop<float, __nv_bfloat16>(const SweepView<float, __nv_bfloat16> &, int,
                                                     const SweepView<float, __nv_bfloat16> &, int, const float *, float *,
                                                     float *, unsigned int *, int *, cudaStream_t);
 template void sweep<float, float>(const SweepView<float, float> &, const float *, float *, int, cudaStream_t);
@@ -869,17 +879,18 @@ __device__ __forceinline__ double warp_dense_dot2(const double *inv, int n, int 
 // block's own writes).  Sweeps use the same two-stage row pipeline as the
 // grid kernels.
 constexpr int DEEP_THREADS = 256;
+constexpr int DEEP_PF = 8;   // row entries prefetched a level ahead (register budget of the deep kernel)
 
 template <typename T, typename V>
 __device__ __forceinline__ void deep_sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag) {
     const int tid = threadIdx.x, nthr = DEEP_THREADS;
     RowA<T> a0 = row_a(S, S.dlev, 0, tid, with_diag), a1 = row_a(S, S.dlev, 1, tid, with_diag);
-    RowB<T, V> b0 = row_b<0>(S, a0, in);
+    RowB<T, V, DEEP_PF> b0 = row_b<0, T, V, DEEP_PF>(S, a0, in);
     for (int l = 0; l < S.nlev; ++l) {
-        const RowB<T, V> b1 = row_b<0>(S, a1, in);
+        const RowB<T, V, DEEP_PF> b1 = row_b<0, T, V, DEEP_PF>(S, a1, in);
         const RowA<T> a2 = row_a(S, S.dlev, l + 2, tid, with_diag);
         if (a0.t >= 0) {
-            out[a0.i] = row_value<false, T, V>(S, a0, b0, out, with_diag);
+            out[a0.i] = row_value<false, T, V, DEEP_PF>(S, a0, b0, out, with_diag);
             const int e = S.dlev[l + 1];
             for (int t = a0.t + nthr; t < e; t += nthr) {
                 const int i = S.rows[t];

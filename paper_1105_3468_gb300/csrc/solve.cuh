@@ -67,9 +67,18 @@ void sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag, cudaStr
 // launch: y = F^{-1} in (schedule levels of F), out = B^{-1} y, with a
 // bounded grid barrier between levels.  bar: 2 device words (zeroed), err:
 // device word set when a barrier wait gives up.
+// Returns the variant that ran (SWEEP_KIND_*).
 template <typename T, typename V>
-void sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
-                     T *y, T *out, unsigned int *bar, int *err, cudaStream_t s);
+int sweep_pair_coop(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in,
+                    T *y, T *out, unsigned int *bar, int *err, cudaStream_t s);
+// Smoother variants, as amg_get_sweep_kind reports them.
+constexpr int SWEEP_KIND_LEVELS = 0;            // one launch per schedule level
+constexpr int SWEEP_KIND_BLOCK = 1;             // one block, block barrier
+constexpr int SWEEP_KIND_CLUSTER_GRID = 2;      // a grid of <= 8 blocks run as one cluster
+constexpr int SWEEP_KIND_GRID = 3;              // cooperative grid, grid barrier
+constexpr int SWEEP_KIND_DSM_REPLICATED = 4;    // one cluster, vectors replicated in every CTA's shared memory
+constexpr int SWEEP_KIND_DATAFLOW = 5;          // cooperative dataflow solve
+constexpr int SWEEP_KIND_TILES = 6;             // grid tiles (finest level, natural-order stencil)
 template <typename T, typename V>
 void sweep_pair_df(const SweepView<T, V> &F, int f_diag, const SweepView<T, V> &B, int b_diag, const T *in, T *y,
                    T *out, unsigned int *bar, int *err, cudaStream_t s);
