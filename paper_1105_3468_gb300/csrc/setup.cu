@@ -9,6 +9,7 @@
 // intrinsics (__dadd_rn, __dmul_rn, ...) so that no multiply-add is fused:
 // the results are bit-identical to the plain sequential definition.
 #include "internal.cuh"
+#include "devsync.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -1057,27 +1058,293 @@ __global__ void k_iota2(int n, int *a, int *b) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = b[i] = i;
 }
 
+// ------------------------------------------------------------------ blocked Gauss-Jordan
+// The same elimination in blocks of GJB steps.  Panel (one cooperative
+// launch per block of steps [k0, ke)): for each step k the pivot search over
+// the panel column k, then the pivot row R brought to step k over the
+// columns j >= ke (the block's earlier steps q < k applied with R's
+// multipliers m_Rq, which sit in R's panel columns) and divided, kept in
+// Ub[k - k0], then the panel columns (k, ke) of every other row updated.
+// Trailing update (one launch): every value m_ij, j >= ke, goes through the
+// block's steps in ascending order, m_ij - m_iq u_qj as one fused
+// multiply-add, skipped when either factor is zero, exactly as the
+// one-step-at-a-time elimination does; a pivot row of the block starts from
+// its divided value after its own step.  Right-part columns of rows not yet
+// pivoted are zero in every pivot row and are not visited.  The inverse is
+// the one of the unblocked elimination bit for bit in its nonzero values.
+constexpr int GJB = 64;            // steps per block
+constexpr int GJ_PANEL_THREADS = 256;
+
+__device__ __forceinline__ void gj_reduce_parts(const GjPart *parts, int nparts, double &best, int &bl, int &br) {
+    __shared__ double sv[GJ_PANEL_THREADS / 32];
+    __shared__ int sl[GJ_PANEL_THREADS / 32], sr[GJ_PANEL_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double b = -1.0;
+    int l = INT_MAX, r = -1;
+    for (int g = tid; g < nparts; g += blockDim.x) {
+        const double v = __ldcg(&parts[g].v);
+        const int gl = __ldcg(&parts[g].l), gr = __ldcg(&parts[g].r);
+        if (gj_better(v, gl, b, l)) { b = v; l = gl; r = gr; }
+    }
+    for (int off = 16; off; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, b, off);
+        const int ol = __shfl_down_sync(0xffffffffu, l, off);
+        const int orr = __shfl_down_sync(0xffffffffu, r, off);
+        if (gj_better(ob, ol, b, l)) { b = ob; l = ol; r = orr; }
+    }
+    if (lane == 0) { sv[warp] = b; sl[warp] = l; sr[warp] = r; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int q = 1; q < (int)blockDim.x / 32; ++q)
+            if (gj_better(sv[q], sl[q], sv[0], sl[0])) { sv[0] = sv[q]; sl[0] = sl[q]; sr[0] = sr[q]; }
+    }
+    __syncthreads();
+    best = sv[0];
+    bl = sl[0];
+    br = sr[0];
+    __syncthreads();
+}
+
+// This block's candidate for the pivot of column c: the largest |m_ic| over
+// its rows i with pos[i] > kmin (first logical position on ties).
+__device__ __forceinline__ void gj_block_candidate(int n, int c, int kmin, const double *M, const int *pos, int r0,
+                                                   int r1, GjPart *out) {
+    __shared__ double sv[GJ_PANEL_THREADS / 32];
+    __shared__ int sl[GJ_PANEL_THREADS / 32], sr[GJ_PANEL_THREADS / 32];
+    const size_t w = 2 * (size_t)n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double b = -1.0;
+    int l = INT_MAX, r = -1;
+    for (int i = r0 + tid; i < r1; i += blockDim.x) {
+        const int li = __ldcg(pos + i);
+        if (li <= kmin) continue;
+        const double a = fabs(__ldcg(M + (size_t)i * w + c));
+        if (gj_better(a, li, b, l)) { b = a; l = li; r = i; }
+    }
+    for (int off = 16; off; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, b, off);
+        const int ol = __shfl_down_sync(0xffffffffu, l, off);
+        const int orr = __shfl_down_sync(0xffffffffu, r, off);
+        if (gj_better(ob, ol, b, l)) { b = ob; l = ol; r = orr; }
+    }
+    if (lane == 0) { sv[warp] = b; sl[warp] = l; sr[warp] = r; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int q = 1; q < (int)blockDim.x / 32; ++q)
+            if (gj_better(sv[q], sl[q], sv[0], sl[0])) { sv[0] = sv[q]; sl[0] = sl[q]; sr[0] = sr[q]; }
+        out[blockIdx.x] = GjPart{sv[0], sl[0] == INT_MAX ? n : sl[0], sr[0]};
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(GJ_PANEL_THREADS) k_gj_panel(int n, int k0, int kb, double *M, int *perm, int *pos,
+                                                               double *Ub, GjPart *parts, int *breakdown,
+                                                               unsigned int *bar, int *err) {
+    const size_t w = 2 * (size_t)n;
+    const int ke = k0 + kb;
+    const size_t wu = w - (size_t)ke;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const int rpb = (n + gridDim.x - 1) / gridDim.x;
+    const int r0 = min(n, blockIdx.x * rpb), r1 = min(n, r0 + rpb);
+    gj_block_candidate(n, k0, k0 - 1, M, pos, r0, r1, parts);
+    grid_barrier(bar, err);
+    for (int k = k0; k < ke; ++k) {
+        if (*(volatile int *)err) return;
+        double best;
+        int p, R;
+        gj_reduce_parts(parts, gridDim.x, best, p, R);
+        if (!(best > 0.0) || !isfinite(best)) {      // singular: keep position k (the result is flagged)
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(breakdown, 1);
+            p = k;
+            R = __ldcg(perm + k);                     // perm[k] is only written below, by block 0
+        }
+        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const int rk = perm[k];
+            perm[k] = R; perm[p] = rk;
+            pos[R] = k; pos[rk] = p;
+        }
+        // the pivot row: to step k and divided
+        double *row = M + (size_t)R * w;
+        const double d = __ldcg(row + k);
+        for (size_t j = (size_t)k + 1 + gt; j < w; j += nt) {
+            double v = __ldcg(row + j);
+            if (j >= (size_t)ke) {
+                for (int q = k0; q < k; ++q) {
+                    const double f = __ldcg(row + q);
+                    const double u = __ldcg(Ub + (size_t)(q - k0) * wu + (j - ke));
+                    if (gj_nonzero(f) && gj_nonzero(u)) v = __fma_rn(-f, u, v);
+                }
+            }
+            v = __ddiv_rn(v, d);
+            row[j] = v;
+            if (j >= (size_t)ke) Ub[(size_t)(k - k0) * wu + (j - ke)] = v;
+        }
+        grid_barrier(bar, err);
+        // the panel columns (k, ke) of every other row; this block's rows
+        const int pw = ke - k - 1;
+        if (pw > 0) {
+            for (int t = threadIdx.x; t < (r1 - r0) * pw; t += blockDim.x) {
+                const int i = r0 + t / pw;
+                if (i == R) continue;
+                const size_t j = (size_t)k + 1 + t % pw;
+                // (a row that was an earlier pivot was written by every block: read past L1)
+                const double f = __ldcg(M + (size_t)i * w + k);
+                const double u = __ldcg(row + j);
+                if (gj_nonzero(f) && gj_nonzero(u))
+                    M[(size_t)i * w + j] = __fma_rn(-f, u, __ldcg(M + (size_t)i * w + j));
+            }
+            __syncthreads();
+            gj_block_candidate(n, k + 1, k, M, pos, r0, r1, parts);
+        }
+        grid_barrier(bar, err);
+    }
+}
+
+// Trailing update of a block: a tile of TR rows x TC columns per CTA, each
+// thread 4 x 4 values; the block's multipliers and divided pivot rows are
+// staged in shared memory.  Columns c < n - ke are the left part's
+// columns ke + c, the rest the right-part columns n + perm[l], l < ke.
+constexpr int GJT_R = 64, GJT_C = 64;
+constexpr size_t GJT_SMEM = sizeof(double) * GJB * (GJT_R + GJT_C) + sizeof(size_t) * GJT_C + sizeof(int) * GJT_R;
+
+__global__ void __launch_bounds__(256) k_gj_trailing(int n, int k0, int kb, double *M, const int *perm,
+                                                     const int *pos, const double *Ub) {
+    // dynamic shared memory (GJT_SMEM bytes): ms[q][r] = m_{row r, k0 + q},
+    // us[q][c] = u_{k0 + q, column c}, the physical column of each tile
+    // column, the first step of the block each row takes
+    extern __shared__ __align__(16) unsigned char gjt_raw[];
+    double (*ms)[GJT_R] = reinterpret_cast<double (*)[GJT_R]>(gjt_raw);
+    double (*us)[GJT_C] = reinterpret_cast<double (*)[GJT_C]>(gjt_raw + sizeof(double) * GJB * GJT_R);
+    size_t *cj = reinterpret_cast<size_t *>(gjt_raw + sizeof(double) * GJB * (GJT_R + GJT_C));
+    int *ks = reinterpret_cast<int *>(cj + GJT_C);
+    const size_t w = 2 * (size_t)n;
+    const int ke = k0 + kb;
+    const size_t wu = w - (size_t)ke;
+    const int nleft = n - ke;
+    const int i0 = blockIdx.y * GJT_R, c0 = blockIdx.x * GJT_C;
+    const int tid = threadIdx.x;
+    if (tid < GJT_C) {
+        const int c = c0 + tid;
+        cj[tid] = c < nleft ? (size_t)ke + c : (c < n ? (size_t)n + perm[c - nleft] : (size_t)-1);
+    }
+    if (tid >= 64 && tid < 64 + GJT_R) {
+        const int i = i0 + tid - 64;
+        const int l = i < n ? pos[i] : 0;
+        ks[tid - 64] = (l >= k0 && l < ke) ? l - k0 + 1 : 0;
+    }
+    __syncthreads();
+    for (int e = tid; e < GJB * GJT_R; e += 256) {
+        const int r = e / GJB, q = e % GJB, i = i0 + r;
+        ms[q][r] = (i < n && q < kb) ? M[(size_t)i * w + k0 + q] : 0.0;
+    }
+    for (int e = tid; e < GJB * GJT_C; e += 256) {
+        const int q = e / GJT_C, c = e % GJT_C;
+        const size_t j = cj[c];
+        us[q][c] = (q < kb && j != (size_t)-1) ? Ub[(size_t)q * wu + (j - ke)] : 0.0;
+    }
+    __syncthreads();
+    const int tr = tid / 16, tc = tid % 16;
+    double acc[4][4];
+    int rks[4];
+    bool rin[4], cin[4];
+    size_t rj[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = i0 + tr * 4 + a;
+        rin[a] = i < n;
+        rks[a] = ks[tr * 4 + a];
+        rj[a] = cj[tc * 4 + a];
+        cin[a] = rj[a] != (size_t)-1;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            acc[a][b] = (rin[a] && cin[b]) ? M[(size_t)(i0 + tr * 4 + a) * w + rj[b]] : 0.0;
+    for (int q = 0; q < kb; ++q) {
+        double m[4], u[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) m[a] = ms[q][tr * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) u[b] = us[q][tc * 4 + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const bool ra = q >= rks[a] && gj_nonzero(m[a]);
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (ra && gj_nonzero(u[b])) acc[a][b] = __fma_rn(-m[a], u[b], acc[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if (rin[a] && cin[b]) M[(size_t)(i0 + tr * 4 + a) * w + rj[b]] = acc[a][b];
+}
+
+// Levels with at least this many rows use the blocked elimination.
+constexpr int GJ_BLOCKED_MIN = 256;
+
 void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
     const int n = A.n;
     DBuf<double> M((size_t)n * 2 * n);
     DBuf<int> bd(1), perm(n), pos(n), R(1);
     const int gy = std::max(1, std::min(n, 2 * sm_count()));
-    DBuf<GjPart> parts(gy);
+    DBuf<GjPart> parts(std::max(gy, sm_count()));
     CU(cudaMemsetAsync(bd.get(), 0, sizeof(int), s));
     k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp.get(), A.ci.get(), A.v.get(), M.get());
     CU_LAUNCH("k_dense_from_csr"); count_launch();
     k_iota2<<<grid_for(n, 256), 256, 0, s>>>(n, perm.get(), pos.get());
     CU_LAUNCH("k_iota2"); count_launch();
-    for (int k = 0; k < n; ++k) {
-        const int pb = std::max(1, std::min((2 * n - k - 1 + 1023) / 1024, sm_count()));
-        k_gj_pivot<<<pb, 256, 0, s>>>(n, k, M.get(), perm.get(), pos.get(), parts.get(), k == 0 ? 0 : gy, R.get(),
-                                      bd.get());      // nparts == 0 only at k == 0
-        // columns j > k over x (one thread each per pass), row groups over y
-        const int xb = std::max(1, std::min((2 * n - k - 1 + 255) / 256, 64));
-        k_gj_elim<<<dim3(xb, gy), 256, 0, s>>>(n, k, M.get(), pos.get(), R.get(), parts.get());
-        count_launch(2);
+    if (n >= GJ_BLOCKED_MIN) {
+        static const int panel_blocks = [] {      // co-resident blocks of the cooperative panel kernel
+            int per_sm = 0;
+            CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_panel, GJ_PANEL_THREADS, 0));
+            return sm_count() * std::max(1, std::min(per_sm, 1));
+        }();
+        static const bool trailing_ready = [] {
+            CU(cudaFuncSetAttribute(k_gj_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJT_SMEM));
+            return true;
+        }();
+        (void)trailing_ready;
+        const int G = std::min(panel_blocks, std::max(1, (n + 15) / 16));
+        DBuf<double> Ub((size_t)GJB * 2 * n);
+        DBuf<unsigned int> bar(2);
+        DBuf<int> err(1);
+        CU(cudaMemsetAsync(bar.get(), 0, 2 * sizeof(unsigned int), s));
+        CU(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+        for (int k0 = 0; k0 < n; k0 += GJB) {
+            int kb = std::min(GJB, n - k0);
+            int nn = n;
+            int k0v = k0;
+            double *Mp = M.get(), *Up = Ub.get();
+            int *pp = perm.get(), *qp = pos.get(), *bp = bd.get(), *ep = err.get();
+            GjPart *parts_p = parts.get();
+            unsigned int *barp = bar.get();
+            void *args[] = {&nn, &k0v, &kb, &Mp, &pp, &qp, &Up, &parts_p, &bp, &barp, &ep};
+            CU(cudaLaunchCooperativeKernel((const void *)k_gj_panel, dim3(G), dim3(GJ_PANEL_THREADS), args, 0, s));
+            count_launch();
+            const int ke = k0 + kb;
+            if (ke < 2 * n) {
+                const dim3 grid((n + GJT_C - 1) / GJT_C, (n + GJT_R - 1) / GJT_R);
+                k_gj_trailing<<<grid, 256, GJT_SMEM, s>>>(n, k0, kb, M.get(), perm.get(), pos.get(), Ub.get());
+                CU_LAUNCH("k_gj_trailing"); count_launch();
+            }
+        }
+        if (read_int(err.get(), s)) fail(8, "dense solve of the last level: a grid barrier wait gave up");
+    } else {
+        for (int k = 0; k < n; ++k) {
+            const int pb = std::max(1, std::min((2 * n - k - 1 + 1023) / 1024, sm_count()));
+            k_gj_pivot<<<pb, 256, 0, s>>>(n, k, M.get(), perm.get(), pos.get(), parts.get(), k == 0 ? 0 : gy,
+                                          R.get(), bd.get());      // nparts == 0 only at k == 0
+            // columns j > k over x (one thread each per pass), row groups over y
+            const int xb = std::max(1, std::min((2 * n - k - 1 + 255) / 256, 64));
+            k_gj_elim<<<dim3(xb, gy), 256, 0, s>>>(n, k, M.get(), pos.get(), R.get(), parts.get());
+            count_launch(2);
+        }
+        CU_LAUNCH("k_gj_*");
     }
-    CU_LAUNCH("k_gj_*");
     inv.alloc((size_t)n * n);
     k_extract_inverse<<<grid_for((size_t)n * n, 256), 256, 0, s>>>(n, M.get(), perm.get(), inv.get());
     CU_LAUNCH("k_extract_inverse"); count_launch();
