@@ -1105,20 +1105,20 @@ __device__ __forceinline__ void gj_reduce_parts(const GjPart *parts, int nparts,
     __syncthreads();
 }
 
-// This block's candidate for the pivot of column c: the largest |m_ic| over
-// its rows i with pos[i] > kmin (first logical position on ties).
-__device__ __forceinline__ void gj_block_candidate(int n, int c, int kmin, const double *M, const int *pos, int r0,
-                                                   int r1, GjPart *out) {
+// This block's candidate for the pivot of panel column cq (column k0 + cq)
+// from its shared-memory panel rows: the largest |m_ic| over rows i with
+// logical position > kmin (first logical position on ties).
+__device__ __forceinline__ void gj_panel_candidate(const double *pan, const int *lpos, int cq, int kmin, int r0,
+                                                   int r1, int n, GjPart *out) {
     __shared__ double sv[GJ_PANEL_THREADS / 32];
     __shared__ int sl[GJ_PANEL_THREADS / 32], sr[GJ_PANEL_THREADS / 32];
-    const size_t w = 2 * (size_t)n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double b = -1.0;
     int l = INT_MAX, r = -1;
     for (int i = r0 + tid; i < r1; i += blockDim.x) {
-        const int li = __ldcg(pos + i);
+        const int li = lpos[i - r0];
         if (li <= kmin) continue;
-        const double a = fabs(__ldcg(M + (size_t)i * w + c));
+        const double a = fabs(pan[(size_t)(i - r0) * GJB + cq]);
         if (gj_better(a, li, b, l)) { b = a; l = li; r = i; }
     }
     for (int off = 16; off; off >>= 1) {
@@ -1137,87 +1137,151 @@ __device__ __forceinline__ void gj_block_candidate(int n, int c, int kmin, const
     __syncthreads();
 }
 
+// Panel kernel of the steps [k0, ke), one grid barrier per step.  Block b
+// keeps the panel columns of its rows [r0, r1) in shared memory and its rows'
+// logical positions; it writes every update of a row that is not the step's
+// pivot through to M (a later pivot row is read from there) and writes all
+// back at the end.  Step k: every block reduces the pivot candidates to the
+// same (p, R), reads R's panel values from M and divides them itself (the
+// same operations, so the same bits in every block).  Thread t of block b
+// owns the trailing column ke + t gridDim.x + b for all steps (the FP64 work
+// spread over every SM) and keeps the divided pivot rows' values in that
+// column in registers, so R's trailing value is brought to step k (the
+// block's earlier steps, with R's multipliers) without further global loads,
+// divided, and written to M and Ub.  Then each block updates its rows' panel
+// columns after k and computes its candidate for column k + 1.  parts holds
+// two sets of gridDim.x candidates.  Needs 2n - ke <= gridDim.x * blockDim.x
+// (checked by the launcher).
 __global__ void __launch_bounds__(GJ_PANEL_THREADS) k_gj_panel(int n, int k0, int kb, double *M, int *perm, int *pos,
                                                                double *Ub, GjPart *parts, int *breakdown,
                                                                unsigned int *bar, int *err) {
+    extern __shared__ __align__(16) double gp_sm[];
+    __shared__ int s_R;
     const size_t w = 2 * (size_t)n;
     const int ke = k0 + kb;
     const size_t wu = w - (size_t)ke;
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const int tid = threadIdx.x;
     const int rpb = (n + gridDim.x - 1) / gridDim.x;
-    const int r0 = min(n, blockIdx.x * rpb), r1 = min(n, r0 + rpb);
-    gj_block_candidate(n, k0, k0 - 1, M, pos, r0, r1, parts);
+    const int r0 = min(n, blockIdx.x * rpb), r1 = min(n, r0 + rpb), nr = r1 - r0;
+    double *pan = gp_sm;                                 // [rpb][GJB] this block's rows, panel columns
+    double *prow = pan + (size_t)rpb * GJB;              // [GJB] the pivot row's panel values
+    int *lpos = reinterpret_cast<int *>(prow + GJB);     // [rpb] logical positions of this block's rows
+    for (int e = tid; e < nr * kb; e += blockDim.x)
+        pan[(e / kb) * GJB + e % kb] = M[(size_t)(r0 + e / kb) * w + k0 + e % kb];
+    for (int i = tid; i < nr; i += blockDim.x) lpos[i] = pos[r0 + i];
+    // trailing columns interleaved over the blocks (each SM gets a share of
+    // the pivot row's FP64 work): thread (b, t) owns column ke + t G + b
+    const size_t jt = (size_t)ke + (size_t)tid * gridDim.x + blockIdx.x;
+    const bool has_col = jt < w;
+    double ucol[GJB];
+#pragma unroll
+    for (int q = 0; q < GJB; ++q) ucol[q] = 0.0;
+    __syncthreads();
+    // candidates of the pivot of column c in parts[(c & 1) G + b]: a block
+    // may write the next column's while another still reduces this one's
+    const int G = gridDim.x;
+    gj_panel_candidate(pan, lpos, 0, k0 - 1, r0, r1, n, parts + (size_t)(k0 & 1) * G);
     grid_barrier(bar, err);
     for (int k = k0; k < ke; ++k) {
         if (*(volatile int *)err) return;
+        const int kq = k - k0;
         double best;
         int p, R;
-        gj_reduce_parts(parts, gridDim.x, best, p, R);
-        if (!(best > 0.0) || !isfinite(best)) {      // singular: keep position k (the result is flagged)
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(breakdown, 1);
+        gj_reduce_parts(parts + (size_t)(k & 1) * G, G, best, p, R);
+        if (!(best > 0.0) || !isfinite(best)) {      // singular: keep position k, no swap (the result is flagged)
+            if (blockIdx.x == 0 && tid == 0) atomicExch(breakdown, 1);
             p = k;
-            R = __ldcg(perm + k);                     // perm[k] is only written below, by block 0
+            if (tid == 0) s_R = -1;
+            __syncthreads();
+            for (int i = tid; i < nr; i += blockDim.x)      // the row at position k, if it is one of ours
+                if (lpos[i] == k) s_R = r0 + i;
+            __syncthreads();
+            R = s_R >= 0 ? s_R : __ldcg(perm + k);           // perm[k] is only written by block 0, below
         }
         __syncthreads();
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (blockIdx.x == 0 && tid == 0) {
             const int rk = perm[k];
             perm[k] = R; perm[p] = rk;
             pos[R] = k; pos[rk] = p;
         }
-        // the pivot row: to step k and divided
-        double *row = M + (size_t)R * w;
-        const double d = __ldcg(row + k);
-        for (size_t j = (size_t)k + 1 + gt; j < w; j += nt) {
-            double v = __ldcg(row + j);
-            if (j >= (size_t)ke) {
-                for (int q = k0; q < k; ++q) {
-                    const double f = __ldcg(row + q);
-                    const double u = __ldcg(Ub + (size_t)(q - k0) * wu + (j - ke));
+        for (int i = tid; i < nr; i += blockDim.x) {     // the row at k moves to p, R to k
+            if (lpos[i] == k) lpos[i] = p;
+            if (r0 + i == R) lpos[i] = k;
+        }
+        // the pivot row's panel values and, for this thread's column, its trailing value
+        double v = has_col ? __ldcg(M + (size_t)R * w + jt) : 0.0;
+        for (int q = tid; q < kb; q += blockDim.x) prow[q] = __ldcg(M + (size_t)R * w + k0 + q);
+        __syncthreads();
+        const double d = prow[kq];
+        if (has_col) {
+#pragma unroll
+            for (int q = 0; q < GJB; ++q) {
+                if (q < kq) {
+                    const double f = prow[q], u = ucol[q];
                     if (gj_nonzero(f) && gj_nonzero(u)) v = __fma_rn(-f, u, v);
                 }
             }
             v = __ddiv_rn(v, d);
-            row[j] = v;
-            if (j >= (size_t)ke) Ub[(size_t)(k - k0) * wu + (j - ke)] = v;
+            M[(size_t)R * w + jt] = v;
+            Ub[(size_t)kq * wu + (jt - ke)] = v;
+#pragma unroll
+            for (int q = 0; q < GJB; ++q)
+                if (q == kq) ucol[q] = v;
         }
-        grid_barrier(bar, err);
-        // the panel columns (k, ke) of every other row; this block's rows
-        const int pw = ke - k - 1;
-        if (pw > 0) {
-            for (int t = threadIdx.x; t < (r1 - r0) * pw; t += blockDim.x) {
-                const int i = r0 + t / pw;
-                if (i == R) continue;
-                const size_t j = (size_t)k + 1 + t % pw;
-                // (a row that was an earlier pivot was written by every block: read past L1)
-                const double f = __ldcg(M + (size_t)i * w + k);
-                const double u = __ldcg(row + j);
-                if (gj_nonzero(f) && gj_nonzero(u))
-                    M[(size_t)i * w + j] = __fma_rn(-f, u, __ldcg(M + (size_t)i * w + j));
+        __syncthreads();                                   // prow[q < kq] read; now the panel part
+        const bool own = R >= r0 && R < r1;                // this block holds the pivot row
+        for (int q = kq + 1 + tid; q < kb; q += blockDim.x) {
+            const double u = __ddiv_rn(prow[q], d);
+            prow[q] = u;
+            // (only the shared copy: other blocks may still be reading R's
+            // panel values from M in this step; written back at the end)
+            if (own) pan[(size_t)(R - r0) * GJB + q] = u;
+        }
+        __syncthreads();
+        const int pw = kb - kq - 1;                        // panel columns after k
+        for (int e = tid; e < nr * pw; e += blockDim.x) {
+            const int li = e / pw, i = r0 + li;
+            if (i == R) continue;
+            const int c = kq + 1 + e % pw;
+            double *pi = pan + (size_t)li * GJB;
+            const double f = pi[kq], u = prow[c];
+            if (gj_nonzero(f) && gj_nonzero(u)) {
+                const double nv = __fma_rn(-f, u, pi[c]);
+                pi[c] = nv;
+                M[(size_t)i * w + k0 + c] = nv;
             }
-            __syncthreads();
-            gj_block_candidate(n, k + 1, k, M, pos, r0, r1, parts);
         }
+        __syncthreads();
+        if (pw > 0) gj_panel_candidate(pan, lpos, kq + 1, k, r0, r1, n, parts + (size_t)((k + 1) & 1) * G);
         grid_barrier(bar, err);
     }
+    for (int e = tid; e < nr * kb; e += blockDim.x)
+        M[(size_t)(r0 + e / kb) * w + k0 + e % kb] = pan[(e / kb) * GJB + e % kb];
 }
 
-// Trailing update of a block: a tile of TR rows x TC columns per CTA, each
-// thread 4 x 4 values; the block's multipliers and divided pivot rows are
-// staged in shared memory.  Columns c < n - ke are the left part's
-// columns ke + c, the rest the right-part columns n + perm[l], l < ke.
-constexpr int GJT_R = 64, GJT_C = 64;
-constexpr size_t GJT_SMEM = sizeof(double) * GJB * (GJT_R + GJT_C) + sizeof(size_t) * GJT_C + sizeof(int) * GJT_R;
+// Trailing update of a block: a tile of GJT_R rows x GJT_C columns per CTA;
+// thread (tr, tc) updates rows tr + 16 a (a < 4) and columns tc + 16 b (b <
+// 8).  The block's multipliers and divided pivot rows are staged in shared
+// memory.  Columns c < n - ke are the left part's columns ke + c, the rest
+// the right-part columns n + perm[l], l < ke.  Every value takes the block's
+// steps in ascending order as one fused multiply-add each (a pivot row of the
+// block only the steps after its own); a product with a zero factor is not
+// skipped here, which changes at most the sign of a zero value, never a
+// nonzero one, and no later step tells the two zeros apart (the tests for
+// zero ignore the sign).  A step whose multipliers or pivot-row values are
+// all zero in the tile is skipped as a whole.
+constexpr int GJT_R = 64, GJT_C = 128;
+constexpr size_t GJT_SMEM = sizeof(double) * GJB * (GJT_R + GJT_C) + sizeof(size_t) * GJT_C + sizeof(int) * GJT_R +
+                            2 * sizeof(int) * GJB;
 
 __global__ void __launch_bounds__(256) k_gj_trailing(int n, int k0, int kb, double *M, const int *perm,
                                                      const int *pos, const double *Ub) {
-    // dynamic shared memory (GJT_SMEM bytes): ms[q][r] = m_{row r, k0 + q},
-    // us[q][c] = u_{k0 + q, column c}, the physical column of each tile
-    // column, the first step of the block each row takes
     extern __shared__ __align__(16) unsigned char gjt_raw[];
     double (*ms)[GJT_R] = reinterpret_cast<double (*)[GJT_R]>(gjt_raw);
     double (*us)[GJT_C] = reinterpret_cast<double (*)[GJT_C]>(gjt_raw + sizeof(double) * GJB * GJT_R);
     size_t *cj = reinterpret_cast<size_t *>(gjt_raw + sizeof(double) * GJB * (GJT_R + GJT_C));
     int *ks = reinterpret_cast<int *>(cj + GJT_C);
+    int *mnz = ks + GJT_R, *unz = mnz + GJB;       // per step: some multiplier / pivot-row value nonzero
     const size_t w = 2 * (size_t)n;
     const int ke = k0 + kb;
     const size_t wu = w - (size_t)ke;
@@ -1228,59 +1292,75 @@ __global__ void __launch_bounds__(256) k_gj_trailing(int n, int k0, int kb, doub
         const int c = c0 + tid;
         cj[tid] = c < nleft ? (size_t)ke + c : (c < n ? (size_t)n + perm[c - nleft] : (size_t)-1);
     }
-    if (tid >= 64 && tid < 64 + GJT_R) {
-        const int i = i0 + tid - 64;
+    if (tid < GJT_R) {
+        const int i = i0 + tid;
         const int l = i < n ? pos[i] : 0;
-        ks[tid - 64] = (l >= k0 && l < ke) ? l - k0 + 1 : 0;
+        ks[tid] = (l >= k0 && l < ke) ? l - k0 + 1 : 0;
     }
+    if (tid < GJB) { mnz[tid] = 0; unz[tid] = 0; }
     __syncthreads();
     for (int e = tid; e < GJB * GJT_R; e += 256) {
         const int r = e / GJB, q = e % GJB, i = i0 + r;
-        ms[q][r] = (i < n && q < kb) ? M[(size_t)i * w + k0 + q] : 0.0;
+        const double v = (i < n && q < kb) ? M[(size_t)i * w + k0 + q] : 0.0;
+        ms[q][r] = v;
+        if (gj_nonzero(v)) mnz[q] = 1;
     }
     for (int e = tid; e < GJB * GJT_C; e += 256) {
         const int q = e / GJT_C, c = e % GJT_C;
         const size_t j = cj[c];
-        us[q][c] = (q < kb && j != (size_t)-1) ? Ub[(size_t)q * wu + (j - ke)] : 0.0;
+        const double v = (q < kb && j != (size_t)-1) ? Ub[(size_t)q * wu + (j - ke)] : 0.0;
+        us[q][c] = v;
+        if (gj_nonzero(v)) unz[q] = 1;
     }
     __syncthreads();
     const int tr = tid / 16, tc = tid % 16;
-    double acc[4][4];
+    double acc[4][8];
     int rks[4];
-    bool rin[4], cin[4];
-    size_t rj[4];
+    bool rin[4], cin[8];
+    size_t rj[8];
+    int kmax = 0;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int i = i0 + tr * 4 + a;
-        rin[a] = i < n;
-        rks[a] = ks[tr * 4 + a];
-        rj[a] = cj[tc * 4 + a];
-        cin[a] = rj[a] != (size_t)-1;
+        rin[a] = i0 + tr + 16 * a < n;
+        rks[a] = ks[tr + 16 * a];
+        kmax = max(kmax, rks[a]);
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        rj[b] = cj[tc + 16 * b];
+        cin[b] = rj[b] != (size_t)-1;
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            acc[a][b] = (rin[a] && cin[b]) ? M[(size_t)(i0 + tr * 4 + a) * w + rj[b]] : 0.0;
+        for (int b = 0; b < 8; ++b)
+            acc[a][b] = (rin[a] && cin[b]) ? M[(size_t)(i0 + tr + 16 * a) * w + rj[b]] : 0.0;
     for (int q = 0; q < kb; ++q) {
-        double m[4], u[4];
+        if (!mnz[q] || !unz[q]) continue;             // uniform over the CTA
+        double m[4], u[8];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) m[a] = ms[q][tr * 4 + a];
+        for (int a = 0; a < 4; ++a) m[a] = ms[q][tr + 16 * a];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) u[b] = us[q][tc * 4 + b];
+        for (int b = 0; b < 8; ++b) u[b] = us[q][tc + 16 * b];
+        if (q >= kmax) {                              // no pivot row of the block still before its step
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const bool ra = q >= rks[a] && gj_nonzero(m[a]);
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (ra && gj_nonzero(u[b])) acc[a][b] = __fma_rn(-m[a], u[b], acc[a][b]);
+                for (int b = 0; b < 8; ++b) acc[a][b] = __fma_rn(-m[a], u[b], acc[a][b]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (q >= rks[a]) {
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) acc[a][b] = __fma_rn(-m[a], u[b], acc[a][b]);
+                }
         }
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            if (rin[a] && cin[b]) M[(size_t)(i0 + tr * 4 + a) * w + rj[b]] = acc[a][b];
+        for (int b = 0; b < 8; ++b)
+            if (rin[a] && cin[b]) M[(size_t)(i0 + tr + 16 * a) * w + rj[b]] = acc[a][b];
 }
 
 // Levels with at least this many rows use the blocked elimination.
@@ -1298,17 +1378,22 @@ void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
     k_iota2<<<grid_for(n, 256), 256, 0, s>>>(n, perm.get(), pos.get());
     CU_LAUNCH("k_iota2"); count_launch();
     if (n >= GJ_BLOCKED_MIN) {
-        static const int panel_blocks = [] {      // co-resident blocks of the cooperative panel kernel
-            int per_sm = 0;
-            CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_panel, GJ_PANEL_THREADS, 0));
-            return sm_count() * std::max(1, std::min(per_sm, 1));
-        }();
-        static const bool trailing_ready = [] {
+        // panel: one block per SM at most (its threads keep 64 FP64 values each
+        // in registers), enough threads for one trailing column each
+        const int G = std::min(sm_count(), std::max(1, (n + 15) / 16));
+        const int rpb = (n + G - 1) / G;
+        const size_t psmem = sizeof(double) * ((size_t)rpb * GJB + GJB) + sizeof(int) * (size_t)rpb;
+        static const bool attrs = [] {
             CU(cudaFuncSetAttribute(k_gj_trailing, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJT_SMEM));
+            CU(cudaFuncSetAttribute(k_gj_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
             return true;
         }();
-        (void)trailing_ready;
-        const int G = std::min(panel_blocks, std::max(1, (n + 15) / 16));
+        (void)attrs;
+        int per_sm = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_panel, GJ_PANEL_THREADS, psmem));
+        if (per_sm < 1 || psmem > 200 * 1024 || 2 * (size_t)n > (size_t)G * GJ_PANEL_THREADS + GJB ||
+            (size_t)2 * G > parts.n)
+            fail(4, "dense solve of the last level: blocked elimination does not fit");
         DBuf<double> Ub((size_t)GJB * 2 * n);
         DBuf<unsigned int> bar(2);
         DBuf<int> err(1);
@@ -1323,14 +1408,11 @@ void dense_inverse(const DCsr &A, DBuf<double> &inv, cudaStream_t s) {
             GjPart *parts_p = parts.get();
             unsigned int *barp = bar.get();
             void *args[] = {&nn, &k0v, &kb, &Mp, &pp, &qp, &Up, &parts_p, &bp, &barp, &ep};
-            CU(cudaLaunchCooperativeKernel((const void *)k_gj_panel, dim3(G), dim3(GJ_PANEL_THREADS), args, 0, s));
+            CU(cudaLaunchCooperativeKernel((const void *)k_gj_panel, dim3(G), dim3(GJ_PANEL_THREADS), args, psmem, s));
             count_launch();
-            const int ke = k0 + kb;
-            if (ke < 2 * n) {
-                const dim3 grid((n + GJT_C - 1) / GJT_C, (n + GJT_R - 1) / GJT_R);
-                k_gj_trailing<<<grid, 256, GJT_SMEM, s>>>(n, k0, kb, M.get(), perm.get(), pos.get(), Ub.get());
-                CU_LAUNCH("k_gj_trailing"); count_launch();
-            }
+            const dim3 grid((n + GJT_C - 1) / GJT_C, (n + GJT_R - 1) / GJT_R);
+            k_gj_trailing<<<grid, 256, GJT_SMEM, s>>>(n, k0, kb, M.get(), perm.get(), pos.get(), Ub.get());
+            CU_LAUNCH("k_gj_trailing"); count_launch();
         }
         if (read_int(err.get(), s)) fail(8, "dense solve of the last level: a grid barrier wait gave up");
     } else {
