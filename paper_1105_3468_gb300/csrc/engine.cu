@@ -55,6 +55,10 @@ struct Level {
     DBuf<float> inv32;                    // FP32 copy for the FP32 / BF16 V-cycles
     // SELL-32 copies for the outer FP64 SpMV (level 0 only)
     Sell sell, sellT;
+    // SELL-32 copy for the V-cycle's forward residual of a level with at
+    // least RSELL_MIN rows (FP64 values in the FP64 V-cycle, else FP32 in rsv32)
+    Sell rsell;
+    DBuf<float> rsv32;
     // workspace (vector type of the V-cycle, allocated as bytes)
     DBuf<char> wt, wy, wr, wres, wh, wg, wf;
     int wy_sent = 0;                      // element size of the sentinel wy holds (dataflow sweeps), 0: none
@@ -405,6 +409,10 @@ static void tune_sell(Sell &SL, const amg_options_t &o, cudaStream_t s) {
 
 // frozen (amg_update_values): the previous hierarchy's per-level, per-pass
 // maps; levels keep the same shape, only the numbers are recomputed.
+// Levels with at least this many rows keep a SELL-32 copy for the V-cycle's
+// forward residual (smaller ones are bound by launch latency).
+constexpr int RSELL_MIN = 32768;
+
 static void build_tiles(amg_handle *h, cudaStream_t s);
 
 static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
@@ -482,6 +490,18 @@ static void setup_impl(amg_handle *h, const amg_csr_t *Ain,
         h->adjoint_ready = true;
     }
     build_tiles(h, s);
+    // SELL-32 copies of the larger levels for the V-cycle's forward residuals
+    for (size_t l = 0; l < h->lev.size(); ++l) {
+        Level &L = *h->lev[l];
+        if (L.dense || L.ilut_level || L.A.n < RSELL_MIN) continue;
+        build_sell(L.A, L.A.v.get(), L.rsell, s);
+        if (o.vcycle_prec != AMG_FP64) {
+            L.rsv32.alloc((size_t)L.rsell.padded);
+            cast_f64_f32(L.rsell.v.get(), L.rsv32.get(), (size_t)L.rsell.padded, s);
+            CU(cudaStreamSynchronize(s));
+            L.rsell.v.release();
+        }
+    }
     // SELL-32 copies of A (and A^T) for the outer FP64 products
     build_sell(h->lev[0]->A, h->lev[0]->A.v.get(), h->lev[0]->sell, s);
     if (o.build_adjoint) build_sell(h->lev[0]->AT, h->lev[0]->AT.v.get(), h->lev[0]->sellT, s);
@@ -659,6 +679,16 @@ struct VCycle {
     // the small residual of smooth errors of a near-singular diffusion
     // operator, which the coarse correction needs).
     void residual(int l, bool tr, const T *x, const T *b, T *r) {
+        Level &Lr = L(l);
+        if (!tr && Lr.rsell.n > 0) {              // SELL-32 copy of a larger level
+            if constexpr (std::is_same<T, double>::value)
+                level_residual_sell<double, double>(Lr.rsell.n, Lr.rsell.ptr.get(), Lr.rsell.ci.get(),
+                                                    Lr.rsell.v.get(), x, b, r, s);
+            else
+                level_residual_sell<float, float>(Lr.rsell.n, Lr.rsell.ptr.get(), Lr.rsell.ci.get(),
+                                                  Lr.rsv32.get(), x, b, r, s);
+            return;
+        }
         if constexpr (std::is_same<V, __nv_bfloat16>::value) {
             Level &Lv = L(l);
             const DCsr &M = tr ? Lv.AT : Lv.A;

@@ -61,6 +61,10 @@ void sell_spmv(int n, int nslices, const int64_t *ptr, const int *ci, const doub
 
 template <typename T, typename V>
 void level_residual(const LevelMats<V> &M, const T *x, const T *b, T *r, cudaStream_t s);
+// The same from a SELL-32 copy (each row summed in stored order).
+template <typename T, typename V>
+void level_residual_sell(int n, const int64_t *ptr, const int *ci, const V *v, const T *x, const T *b, T *r,
+                         cudaStream_t s);
 template <typename T, typename V>
 void sweep(const SweepView<T, V> &S, const T *in, T *out, int with_diag, cudaStream_t s);
 // Both triangular solves of one smoother application in one cooperative
