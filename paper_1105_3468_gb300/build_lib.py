@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libamg_gb.so")
-SOURCES = ["prims.cu", "setup.cu", "solve.cu", "tiles.cu", "engine.cu", "noalloc.cu", "ilut.cu"]
+SOURCES = ["prims.cu", "setup.cu", "solve.cu", "tiles.cu", "sell_residual.cu", "engine.cu", "noalloc.cu", "ilut.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                 "-I", os.path.join(ROOT, "include")]
