@@ -49,6 +49,11 @@ def test_host_only_calls(lib):
     assert out.value is None
     assert "null" in pkg.lib().amg_last_error().decode()
     assert "sm_103a" in pkg.amg_version()
+    assert o.persistent == 5      # grid tiles on a stencil finest level, else as 3
+    info = (C.c_int64 * 8)()
+    kind = (C.c_int32 * 2)()
+    assert lib.amg_get_tile_grid(None, info) == pkg.AMG_ERR_INVALID_ARG
+    assert lib.amg_get_sweep_kind(None, 0, kind) == pkg.AMG_ERR_INVALID_ARG
 
 
 def test_struct_sizes_match_header():
